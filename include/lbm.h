@@ -1,0 +1,180 @@
+/*
+ * lbm.h -- C ABI of the B300 (sm_103a) lattice-Boltzmann hot path.
+ *
+ * One time step is the IMEXLBM update of arxiv 2201.11330: the local BGK
+ * collision of Eq. (collision) with the paper's time discretisation
+ * (omega = 1/(tau_paper + 1/2)), the incompressible equilibrium of Eq.
+ * (incompressible_feq) (or Eq. (feq) on request), fused with propagation
+ * Eq. (propagation) and the boundary conditions of Sec. 2.2 (half-way
+ * bounce-back Eq. (bb)), a moving lid and periodic faces.  Steps run in the
+ * order Collision -> BoundaryCondition -> Propagation -> PostProcessing of
+ * Sec. 3.1, fused into one kernel launch per step.
+ *
+ * Conventions shared by every call
+ *   - tau is the STANDARD BGK relaxation time tau_std = tau_paper + 1/2, so
+ *     omega = 1/tau and nu = (tau - 1/2)/3.  lbm_tau_from_paper() converts.
+ *   - Lattice units: c = 1, c_s^2 = 1/3, dt = 1.  Pressure p = c_s^2 sum f.
+ *   - Grids are nx * ny * nz nodes, node index n = x + nx*(y + ny*z);
+ *     2D (D2Q9) uses nz = 1.  N = nx*ny*nz must be below 2^31.
+ *   - Field arrays are structure of arrays: a d-component field is d
+ *     consecutive blocks of N values (component-major).
+ *   - Walls sit half a spacing outside the first and last node of a walled
+ *     axis.  LBM_BC_CAVITY walls every face and moves the +y face ("lid");
+ *     LBM_BC_CHANNEL walls the y faces only (the +y wall may move) with x and
+ *     z periodic; LBM_BC_PERIODIC wraps every axis.  A link crossing the
+ *     moving wall (upstream y >= ny, corners included) gains
+ *     2 t_a rho0 (e_a . U)/c_s^2.
+ *
+ * Memory and streams
+ *   - The library never allocates device memory.  The caller passes one
+ *     device workspace of lbm_workspace_bytes() bytes (any allocator, e.g. a
+ *     torch uint8 tensor), 256-byte aligned, that must outlive the context.
+ *     Every other device pointer is borrowed for the duration of the call
+ *     only, except the force field of lbm_set_force, which is borrowed until
+ *     it is replaced or the context is destroyed.
+ *   - Every kernel is launched on the context's stream (a cudaStream_t passed
+ *     as void*, NULL = legacy default stream).  Calls are asynchronous unless
+ *     they return host values (lbm_reduce, lbm_adjoint*), which synchronise
+ *     that stream.
+ *
+ * Errors: every call returns an lbm_status.  Argument errors are found on the
+ * host before anything is launched and leave the context unchanged.  No call
+ * aborts, throws or prints.  lbm_error_string() gives a static description.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,      /* invalid argument (sizes, tau <= 1/2, NULL, enum) */
+    LBM_ERR_CUDA = -2,     /* a CUDA launch or copy failed */
+    LBM_ERR_UNSTABLE = -3, /* a reduction saw a non-finite value */
+    LBM_ERR_STATE = -4,    /* call not valid in the context's current state */
+    LBM_ERR_NOMEM = -5     /* workspace smaller than required */
+} lbm_status;
+
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 } lbm_lattice;
+
+typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_CAVITY = 1, LBM_BC_CHANNEL = 2 } lbm_bc;
+
+/* Storage of the distributions in HBM.  Arithmetic is FP64 for LBM_F64 and
+ * FP32 otherwise.  The "shifted" forms store f_a - t_a (t_a the lattice
+ * weight), which the incompressible update leaves invariant up to rounding. */
+typedef enum {
+    LBM_F64 = 0,   /* FP64, unshifted */
+    LBM_F32 = 1,   /* FP32, shifted (unshifted with lbm_opts.f32_unshifted) */
+    LBM_F16S = 2,  /* IEEE binary16 of f - t, round to nearest even */
+    LBM_BF16S = 3  /* bfloat16 of f - t, round to nearest even */
+} lbm_storage;
+
+typedef struct {
+    int storage;        /* lbm_storage */
+    int aa;             /* 0: two-lattice pull scheme; 1: single-lattice AA pattern */
+    int compressible;   /* 0: Eq. (incompressible_feq); 1: Eq. (feq) with rho = sum f */
+    int f32_unshifted;  /* LBM_F32 only: store f itself instead of f - t */
+    double rho0;        /* constant density of the incompressible model (> 0) */
+    double lid_u[3];    /* moving-wall velocity (ignored for LBM_BC_PERIODIC) */
+    int has_force;      /* 1: a body-force field will be set with lbm_set_force */
+} lbm_opts;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Defaults: LBM_F32, pull scheme, incompressible, shifted, rho0 = 1, lid 0. */
+void lbm_default_opts(lbm_opts *opts);
+
+/* tau_std = tau_paper + 1/2 (Sec. 3.3: "ome = 1/(tau+0.5)"). */
+double lbm_tau_from_paper(double tau_paper);
+
+/* Bytes of device workspace a context of this shape needs (0 on bad
+ * arguments): the distributions (two lattices for the pull scheme, one for
+ * AA) plus reduction scratch. */
+size_t lbm_workspace_bytes(int lattice, int nx, int ny, int nz, const lbm_opts *opts);
+
+/* Create a context (host memory only).  Sec. 3.3 DataInput/AllocateArrays:
+ * the case is fixed here.  dev_workspace: caller-owned device memory of
+ * `bytes` >= lbm_workspace_bytes(); cuda_stream: cudaStream_t or NULL.
+ * Errors: LBM_ERR_ARG (bad lattice/bc/storage, sizes < 1, nz != 1 for D2Q9,
+ * tau <= 1/2, rho0 <= 0, N >= 2^31, misaligned workspace), LBM_ERR_NOMEM
+ * (workspace too small). */
+int lbm_create(int lattice, int nx, int ny, int nz, double tau, int bc, const lbm_opts *opts,
+               void *dev_workspace, size_t bytes, void *cuda_stream, lbm_ctx **out);
+
+/* Change the stream later calls launch on. */
+int lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
+
+/* Sec. 2.2 / Sec. 3.3 InitUP + Sec. 3.4 InitPDF: f = feq(p, u) at every node.
+ * p: device FP64 pressure field (N values) or NULL for p = 1/3 everywhere;
+ * u: device FP64 velocity field (d*N, component-major) or NULL for u = 0.
+ * Resets the step counter to 0.  When a force is set, the stored state also
+ * holds the first collision (the state is always post-collision). */
+int lbm_init(lbm_ctx *ctx, const double *p, const double *u);
+
+/* Body force (Guo form, trapezoidal): device FP32 field of d*N values,
+ * component-major, borrowed until replaced; NULL removes the force.
+ * Requires opts.has_force = 1 at creation (LBM_ERR_STATE otherwise). */
+int lbm_set_force(lbm_ctx *ctx, const float *force);
+
+/* Moving-wall velocity U (3 values, host).  Takes effect at the next step. */
+int lbm_set_lid(lbm_ctx *ctx, const double *lid_u3);
+
+/* Advance n >= 0 time steps (Sec. 3.1 main loop body), one fused kernel
+ * launch per step. */
+int lbm_step(lbm_ctx *ctx, int64_t n);
+
+/* Steps taken since lbm_init (or the value given to lbm_set_state). */
+int64_t lbm_step_count(const lbm_ctx *ctx);
+
+/* Sec. 3.4 PostProcessing: p = c_s^2 sum f and u = (sum e f + F/2)/rho of
+ * the current step.  p_out: device, N values, or NULL; u_out: device, d*N
+ * values component-major, or NULL.  out_dtype: 0 = FP64, 1 = FP32. */
+int lbm_macroscopic(lbm_ctx *ctx, void *p_out, void *u_out, int out_dtype);
+
+/* Sec. 3.4 Monitor (global part done on the GPU): out[0] = sum_x P (mass,
+ * P = sum_a f_a), out[1..3] = sum_x rho u (momentum), out[4] = sum_x
+ * rho |u|^2 / 2 (kinetic energy), out[5] = max_x |u|.  Per-node terms in the
+ * kernel's arithmetic, cross-block sums in FP64.  out: host, 6 doubles.
+ * Synchronises the stream.  LBM_ERR_UNSTABLE if any result is not finite. */
+int lbm_reduce(lbm_ctx *ctx, double *out);
+
+/* Checkpoint / resume.  The state is the encoded distributions of
+ * lbm_state_bytes() bytes (layout private to the library, stable for a
+ * given shape and options).  dst/src: device. */
+size_t lbm_state_bytes(const lbm_ctx *ctx);
+int lbm_get_state(lbm_ctx *ctx, void *dst, int64_t *step);
+int lbm_set_state(lbm_ctx *ctx, const void *src, int64_t step);
+
+/* Adjoint (not in the paper): gradients of J = rho0/2 sum_x |u(x, T)|^2
+ * after T steps from the current state, with respect to the force field and
+ * the moving-wall velocity.  States are checkpointed every K steps and
+ * recomputed in between.  Incompressible model and pull scheme only.
+ * adj_workspace: device, lbm_adjoint_workspace_bytes(ctx, T, K) bytes.
+ * lbm_adjoint_forward runs the T forward steps (the context ends at step
+ * T) and returns J; lbm_adjoint_backward then fills dJdF (device FP64, d*N,
+ * component-major; may be NULL) and dJdU (host, 3 doubles; may be NULL).
+ * lbm_adjoint does both.  All three synchronise the stream. */
+size_t lbm_adjoint_workspace_bytes(const lbm_ctx *ctx, int64_t T, int64_t K);
+int lbm_adjoint_forward(lbm_ctx *ctx, int64_t T, int64_t K, void *adj_workspace, size_t bytes,
+                        double *J);
+int lbm_adjoint_backward(lbm_ctx *ctx, void *adj_workspace, size_t bytes, double *dJdF,
+                         double *dJdU);
+int lbm_adjoint(lbm_ctx *ctx, int64_t T, int64_t K, void *adj_workspace, size_t bytes,
+                double *J, double *dJdF, double *dJdU);
+
+/* Static description of a status code. */
+const char *lbm_error_string(int status);
+
+/* Free the host-side context (the workspace stays the caller's). */
+void lbm_destroy(lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,313 @@
+"""Pins of the FP64 CPU oracle against facts the paper and the mathematics fix.
+
+None of these tests compares the oracle with itself or with the CUDA path:
+each checks a closed form, an invariant, an analytic flow or a finite
+difference, so that a dropped term, a wrong sign, a wrong index or a
+transposed operand in the oracle fails at least one of them.
+"""
+from fractions import Fraction
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2201_11330_b300 import workloads as W
+
+LATTICES = ["d2q9", "d3q19", "d3q27"]
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.1: the velocity sets
+
+
+def test_d2q9_table_matches_sec2_1():
+    """The D2Q9 matrix and weights equal the ones printed in Sec. 2.1."""
+    rows = {}
+    with open(os.path.join(GOLDEN, "d2q9_table_sec2_1.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, *vals = line.split()
+            rows[key] = vals
+    e, t, opp = oracle.tables("d2q9")
+    assert [int(v) for v in rows["e_x"]] == list(e[:, 0])
+    assert [int(v) for v in rows["e_y"]] == list(e[:, 1])
+    assert np.all(e[:, 2] == 0)
+    want = [float(Fraction(v)) for v in rows["t"]]
+    assert list(t) == want
+    # "opposite of a is m-1-a" (Sec. 2.1)
+    assert list(opp) == list(range(8, -1, -1))
+
+
+@pytest.mark.parametrize("lattice", LATTICES)
+def test_velocity_set_isotropy(lattice):
+    """Weights reproduce the Maxwellian moments up to fourth order, c_s^2 = 1/3."""
+    e, t, opp = oracle.tables(lattice)
+    Q, d = oracle.dims(lattice)
+    assert len(t) == Q == {"d2q9": 9, "d3q19": 19, "d3q27": 27}[lattice]
+    assert len({tuple(v) for v in e}) == Q
+    assert list(opp) == list(range(Q - 1, -1, -1))
+    assert np.all(e[opp] == -e)
+    assert abs(t.sum() - 1) < 1e-15
+    E = e[:, :d].astype(float)
+    assert np.abs(t @ E).max() < 1e-16
+    I = np.eye(d)
+    assert np.abs(np.einsum("a,ai,aj->ij", t, E, E) - I / 3).max() < 1e-15
+    assert np.abs(np.einsum("a,ai,aj,ak->ijk", t, E, E, E)).max() < 1e-16
+    four = np.einsum("a,ai,aj,ak,al->ijkl", t, E, E, E, E)
+    want = (np.einsum("ij,kl->ijkl", I, I) + np.einsum("ik,jl->ijkl", I, I)
+            + np.einsum("il,jk->ijkl", I, I)) / 9
+    assert np.abs(four - want).max() < 1e-15
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.1: equilibria
+
+
+@pytest.mark.parametrize("lattice", LATTICES)
+@pytest.mark.parametrize("compressible", [False, True])
+def test_equilibrium_moments(lattice, compressible):
+    """Zeroth, first and second moments of Eq. (incompressible_feq) / Eq. (feq)."""
+    rng = np.random.default_rng(11)
+    e, t, _ = oracle.tables(lattice)
+    Q, d = oracle.dims(lattice)
+    E = e[:, :d].astype(float)
+    for _ in range(5):
+        P = 1.0 + 0.1 * rng.standard_normal()
+        u = 0.08 * rng.standard_normal(d)
+        rho0 = 1.0 + 0.2 * rng.random()
+        feq = oracle.equilibrium(lattice, P, u, rho0=rho0, compressible=compressible)
+        r = P if compressible else rho0
+        assert abs(feq.sum() - P) < 1e-14
+        assert np.abs(E.T @ feq - r * u).max() < 1e-15
+        second = np.einsum("a,ai,aj->ij", feq, E, E)
+        assert np.abs(second - (P / 3 * np.eye(d) + r * np.outer(u, u))).max() < 1e-14
+
+
+@pytest.mark.parametrize("lattice", LATTICES)
+def test_collision_invariants(lattice):
+    """Eq. (collision) keeps P and j; feq is its fixed point; the force adds F to j."""
+    rng = np.random.default_rng(5)
+    e, t, _ = oracle.tables(lattice)
+    Q, d = oracle.dims(lattice)
+    E = e[:, :d].astype(float)
+    for tau in (0.55, 0.8, 1.7):
+        f = t * (1 + 0.05 * rng.standard_normal(Q))
+        out = oracle.collide_node(lattice, f, tau)
+        assert abs(out.sum() - f.sum()) < 1e-15
+        assert np.abs(E.T @ out - E.T @ f).max() < 1e-15
+        # rest fraction relaxes by exactly (1 - omega) away from equilibrium
+        P = f.sum()
+        u = E.T @ f
+        feq = oracle.equilibrium(lattice, P, u)
+        assert np.abs(out - (feq + (1 - 1 / tau) * (f - feq))).max() < 1e-15
+        assert np.abs(oracle.collide_node(lattice, feq, tau) - feq).max() < 1e-15
+        F = 1e-4 * rng.standard_normal(d)
+        outF = oracle.collide_node(lattice, f, tau, F=F)
+        assert abs(outF.sum() - f.sum()) < 1e-15
+        assert np.abs(E.T @ outF - (E.T @ f + F)).max() < 1e-15
+
+
+# --------------------------------------------------------------------------
+# Whole scheme: invariants
+
+
+@pytest.mark.parametrize("lattice,shape", [("d2q9", (12, 10, 1)), ("d3q19", (6, 5, 7)),
+                                           ("d3q27", (5, 6, 4))])
+@pytest.mark.parametrize("bc", ["cavity", "periodic", "channel"])
+def test_rest_state_is_exact(lattice, shape, bc):
+    """u = 0, no force, resting walls: every population stays at t_a (to round-off)."""
+    nx, ny, nz = shape
+    _, t, _ = oracle.tables(lattice)
+    _, _, f0 = oracle.run(lattice, nx, ny, nz, 0.7, bc, 0, want_f=True)
+    assert np.array_equal(f0, np.repeat(t[:, None], nx * ny * nz, axis=1))
+    p, u, f = oracle.run(lattice, nx, ny, nz, 0.7, bc, 40, want_f=True)
+    assert np.abs(f - f0).max() < 1e-15
+    assert np.abs(u).max() < 1e-15
+
+
+@pytest.mark.parametrize("lattice,shape", [("d2q9", (16, 12, 1)), ("d3q19", (8, 6, 7)),
+                                           ("d3q27", (6, 7, 5))])
+def test_periodic_conservation(lattice, shape):
+    """Periodic streaming + collision conserve sum P and sum j to round-off."""
+    nx, ny, nz = shape
+    Q, d = oracle.dims(lattice)
+    p0, u0 = W.random_smooth_state(nx, ny, nz, d, amp_u=0.05, amp_p=1e-3, seed=3)
+    N = nx * ny * nz
+    p, u = oracle.run(lattice, nx, ny, nz, 0.62, "periodic", 300, p0=p0, u0=u0)
+    assert abs(p.sum() - p0.sum()) / N < 1e-14
+    assert np.abs(u.sum(axis=1) - u0.sum(axis=1)).max() / N < 1e-14
+    # something did happen
+    assert np.abs(u - u0).max() > 1e-4
+
+
+@pytest.mark.parametrize("lattice,shape", [("d2q9", (10, 8, 1)), ("d3q19", (6, 5, 4))])
+def test_uniform_force_momentum_growth(lattice, shape):
+    """Each step adds exactly F per node to the momentum of a periodic box."""
+    nx, ny, nz = shape
+    Q, d = oracle.dims(lattice)
+    N = nx * ny * nz
+    G = np.array([2e-5, -1e-5, 3e-5][:d])
+    F = np.repeat(G[:, None], N, axis=1)
+    for n in (1, 7, 30):
+        p, u = oracle.run(lattice, nx, ny, nz, 0.9, "periodic", n, F=F)
+        # rho0 u = j + F/2, with j = n F after n steps from rest
+        assert np.abs(u.sum(axis=1) - (n + 0.5) * G * N).max() < 1e-16 * N * n + 1e-18
+        assert abs(p.sum() - N / 3) < 1e-14 * N
+
+
+@pytest.mark.parametrize("lattice,shape", [("d2q9", (12, 9, 1)), ("d3q19", (7, 6, 5)),
+                                           ("d3q27", (5, 6, 4))])
+def test_cavity_mass_conservation(lattice, shape):
+    """A closed cavity with a tangential lid keeps its mass (corners included)."""
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    p, u = oracle.run(lattice, nx, ny, nz, 0.6, "cavity", 200, lid=[0.1, 0, 0])
+    assert abs(p.sum() - N / 3) / N < 1e-14
+    assert np.abs(u).max() > 1e-3
+
+
+@pytest.mark.parametrize("lattice", ["d3q19", "d3q27"])
+def test_cavity_mirror_symmetry(lattice):
+    """Lid along +x: the flow is mirror-symmetric about the z mid-plane."""
+    nx, ny, nz = 7, 6, 6
+    p, u = oracle.run(lattice, nx, ny, nz, 0.6, "cavity", 150, lid=[0.1, 0, 0])
+    P = p.reshape(nz, ny, nx)
+    U = u.reshape(3, nz, ny, nx)
+    assert np.abs(U[0] - U[0][::-1]).max() < 1e-15
+    assert np.abs(U[1] - U[1][::-1]).max() < 1e-15
+    assert np.abs(U[2] + U[2][::-1]).max() < 1e-15
+    assert np.abs(P - P[::-1]).max() < 1e-15
+    assert np.abs(U[2]).max() > 1e-5
+
+
+def test_pressure_gauge_invariance():
+    """Incompressible model: shifting P0 by a constant leaves u unchanged."""
+    nx, ny, nz = 8, 7, 6
+    _, u0 = W.random_smooth_state(nx, ny, nz, 3, seed=9)
+    N = nx * ny * nz
+    pa, ua = oracle.run("d3q19", nx, ny, nz, 0.7, "cavity", 60, lid=[0.05, 0, 0],
+                        p0=np.full(N, 1 / 3), u0=u0)
+    pb, ub = oracle.run("d3q19", nx, ny, nz, 0.7, "cavity", 60, lid=[0.05, 0, 0],
+                        p0=np.zeros(N), u0=u0)
+    assert np.abs(ua - ub).max() < 1e-15
+    assert np.abs((pa - pb) - 1 / 3).max() < 1e-14
+
+
+# --------------------------------------------------------------------------
+# Whole scheme: analytic flows
+
+
+def _tg_amplitude(u, n):
+    x, y, _ = W.grid(n, n, 1)
+    k = 2 * math.pi / n
+    mode = -np.cos(k * x) * np.sin(k * y)
+    return (u[0] * mode).sum() / (mode * mode).sum()
+
+
+@pytest.mark.parametrize("compressible", [False, True])
+def test_taylor_green_decay(compressible):
+    """Velocity amplitude decays at nu (kx^2 + ky^2), nu = (tau - 1/2)/3 (within 1%)."""
+    n, tau = 96, 0.8
+    p0, u0 = W.taylor_green_2d(n, n, 0.05)
+    amps = []
+    for T in (100, 900):
+        _, u = oracle.run("d2q9", n, n, 1, tau, "periodic", T, p0=p0, u0=u0,
+                          compressible=compressible)
+        amps.append(_tg_amplitude(u, n))
+    rate = -math.log(amps[1] / amps[0]) / 800
+    assert abs(rate / W.taylor_green_rate(n, n, tau) - 1) < 0.01
+
+
+@pytest.mark.parametrize("lattice", ["d2q9", "d3q19", "d3q27"])
+def test_poiseuille(lattice):
+    """Body-force channel flow: exact parabola at (tau - 1/2)^2 = 3/16; else the
+    same second differences (-G/nu) plus a constant wall slip."""
+    ny, G = 14, 1e-6
+    Q, d = oracle.dims(lattice)
+    for tau in (0.5 + math.sqrt(3 / 16), 0.8):
+        nu = W.viscosity(tau)
+        F = np.zeros((d, ny))
+        F[0] = G
+        steps = int(25 * ny * ny / nu)
+        _, u = oracle.run(lattice, 1, ny, 1, tau, "channel", steps, F=F)
+        ux = u[0]
+        y = np.arange(ny)
+        parabola = G / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+        d2 = ux[2:] - 2 * ux[1:-1] + ux[:-2]
+        assert np.abs(d2 * nu / G + 1).max() < 1e-8
+        slip = ux - parabola
+        assert np.abs(slip - slip.mean()).max() < 1e-9 * parabola.max()
+        if tau < 0.9:
+            assert abs(slip.mean()) > 1e-4 * parabola.max()
+        else:
+            assert np.abs(slip).max() < 1e-9 * parabola.max()
+        assert np.abs(u[1:]).max() < 1e-10 * parabola.max()
+
+
+@pytest.mark.parametrize("lattice", ["d2q9", "d3q19"])
+def test_couette(lattice):
+    """Moving top wall, no force: linear profile U (y + 1/2)/ny for any tau."""
+    ny, U = 12, 0.02
+    for tau in (0.6, 1.3):
+        nu = W.viscosity(tau)
+        _, u = oracle.run(lattice, 1, ny, 1, tau, "channel", int(25 * ny * ny / nu),
+                          lid=[U, 0, 0])
+        y = np.arange(ny)
+        assert np.abs(u[0] - U * (y + 0.5) / ny).max() < 1e-10 * U
+
+
+# --------------------------------------------------------------------------
+# Adjoint: central finite differences of the forward run
+
+
+def _J(lattice, shape, tau, bc, T, lid, F):
+    nx, ny, nz = shape
+    _, u = oracle.run(lattice, nx, ny, nz, tau, bc, T, lid=lid, F=F)
+    return 0.5 * float((u * u).sum())
+
+
+@pytest.mark.parametrize("lattice,shape,bc", [("d3q19", (4, 5, 3), "cavity"),
+                                              ("d2q9", (6, 5, 1), "channel"),
+                                              ("d3q27", (3, 4, 3), "periodic")])
+def test_adjoint_matches_finite_differences(lattice, shape, bc):
+    nx, ny, nz = shape
+    Q, d = oracle.dims(lattice)
+    N = nx * ny * nz
+    tau, T, K = 0.7, 7, 3
+    lid = [0.05, 0.0, 0.01] if bc != "periodic" else None
+    F = W.fourier_force(nx, ny, nz, amplitude=1e-3, seed=4, dims=d, dtype=np.float64)
+    J, gF, gU = oracle.adjoint(lattice, nx, ny, nz, tau, bc, T, K, lid=lid, F=F)
+    assert abs(J - _J(lattice, shape, tau, bc, T, lid, F)) < 1e-15
+    rng = np.random.default_rng(1)
+    for _ in range(2):
+        v = rng.standard_normal((d, N))
+        h = 1e-3 * np.abs(F).max()
+        fd = (_J(lattice, shape, tau, bc, T, lid, F + h * v)
+              - _J(lattice, shape, tau, bc, T, lid, F - h * v)) / (2 * h)
+        assert abs(fd - (gF * v).sum()) <= 1e-7 * abs(fd)
+    if lid is not None:
+        for k in (0, 2):
+            h = 1e-4
+            lp = list(lid); lm = list(lid)
+            lp[k] += h; lm[k] -= h
+            fd = (_J(lattice, shape, tau, bc, T, lp, F) - _J(lattice, shape, tau, bc, T, lm, F)) / (2 * h)
+            assert abs(fd - gU[k]) <= 1e-6 * abs(fd) + 1e-14
+    else:
+        assert np.all(gU == 0)
+
+
+def test_adjoint_checkpoint_interval_invariance():
+    """Recomputing between checkpoints gives the same gradient for any K."""
+    args = ("d3q19", 4, 4, 3, 0.75, "cavity", 9)
+    F = W.fourier_force(4, 4, 3, amplitude=1e-3, seed=2, dtype=np.float64)
+    ref = oracle.adjoint(*args, 1, lid=[0.05, 0, 0], F=F)
+    for K in (2, 4, 9, 20):
+        got = oracle.adjoint(*args, K, lid=[0.05, 0, 0], F=F)
+        assert got[0] == ref[0]
+        assert np.array_equal(got[1], ref[1])
+        assert np.array_equal(got[2], ref[2])
