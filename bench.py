@@ -1,0 +1,476 @@
+"""Benchmark of the fused lattice-Boltzmann step on B300.
+
+Headline workload: D3Q19 lid-driven cavity, 512^3 nodes, Re = 1000, lid
+u = 0.1, AA single-lattice pattern, FP32 arithmetic on FP32 shifted storage.
+A "step" is one time step (one fused stream-collide launch) over the whole
+box.  `value` is whole-job GLUPS (nodes x steps / time / 1e9) summed over
+ranks, timed with CUDA events on the launching stream; the state (10.2 GB)
+is larger than L2, so no flush is needed between steps.
+
+Besides the headline line the same JSON carries: FP16/BF16-shifted storage
+and the two-lattice pull scheme on the same cavity, the D3Q27 768^3
+FP16-shifted AA cavity, the adjoint/forward time ratio (D3Q19 periodic
+128^3, T = 2000, K = 100), the end-to-end rate through the public API with
+host buffers, the roofline of the dominant kernel and the FP64 CPU oracle's
+rate on the host (a baseline only).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUPS & % HBM roofline (D3Q19 FP32 vs FP16-shift); adjoint/forward time ratio"
+Q_OF = {"d2q9": 9, "d3q19": 19, "d3q27": 27}
+BYTES_OF = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
+HEADLINE = dict(lattice="d3q19", n=512, re=1000.0, lid_u=0.1, storage="f32", aa=True)
+
+
+def workload_name(lattice, n, re, storage, aa):
+    scheme = "AA single lattice" if aa else "two-lattice pull"
+    return (f"{lattice.upper()} lid-driven cavity {n}^3, Re={re:g}, lid u=0.1, {scheme}, "
+            f"{storage.upper()} storage, FP{'64' if storage == 'f64' else '32'} arithmetic")
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2201_11330_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel_tag):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and parts[0] == kernel_tag and not line.startswith("#"):
+            if parts[2] == want:
+                return float(parts[1])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas: one independent run per GPU)
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value, world, device):
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# timed runs
+
+
+def timed_steps(lat, steps, warmup, world, per_launch=True):
+    """Run warmup + steps single-step launches; returns total ms (max over
+    ranks) and per-launch event durations split by AA parity."""
+    import torch
+    lat.step(warmup)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    parity = []
+    barrier(world)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for i in range(steps):
+        parity.append(lat.step_count % 2)
+        lat.step(1)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    durs = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    total = ev[0].elapsed_time(ev[steps])
+    return total, durs, parity
+
+
+def make_cavity(lattice, n, re, storage, aa, lid_u=0.1):
+    from paper_2201_11330_b300 import workloads as W
+    from paper_2201_11330_b300.lbm import Lattice
+    c = W.cavity_params(n, re, lid_u)
+    lat = Lattice(lattice, n, n, n, c["tau"], "cavity", storage=storage, aa=aa, lid=c["lid"])
+    lat.init()
+    return lat
+
+
+def run_cavity(lattice, n, re, storage, aa, steps, warmup, world, device):
+    import torch
+    lat = make_cavity(lattice, n, re, storage, aa)
+    total, durs, parity = timed_steps(lat, steps, warmup, world)
+    total = max_over_ranks(total, world, device)
+    N = n ** 3
+    glups = world * N * steps / (total * 1e-3) / 1e9
+    bytes_per_node = 2 * Q_OF[lattice] * BYTES_OF[storage]
+    out = {"glups": glups, "ms_per_step": total / steps, "bytes_per_node": bytes_per_node,
+           "nodes": N}
+    if aa:
+        g = [d for d, p in zip(durs, parity) if p == 0]
+        l = [d for d, p in zip(durs, parity) if p == 1]
+        out["gather_ms"] = statistics.mean(g) if g else None
+        out["local_ms"] = statistics.mean(l) if l else None
+    else:
+        out["pull_ms"] = statistics.mean(durs)
+    r = lat.reduce()
+    out["mass_rel_drift"] = abs(r["mass"] - N) / N
+    out["max_speed"] = r["max_speed"]
+    del lat
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_e2e(n, re, storage, steps, warmup, world, device):
+    """Public API with host buffers: pinned-host initial fields -> device,
+    lbm_init, then per step lbm_step + lbm_reduce (Monitor; 48 B to host),
+    final macroscopic fields -> pinned host.  All inside the timed region."""
+    import torch
+    from paper_2201_11330_b300 import workloads as W
+    from paper_2201_11330_b300.lbm import Lattice
+    c = W.cavity_params(n, re, 0.1)
+    N = n ** 3
+    lat = Lattice("d3q19", n, n, n, c["tau"], "cavity", storage=storage, aa=True, lid=c["lid"])
+    p_host = torch.full((N,), 1.0 / 3.0, dtype=torch.float64).pin_memory()
+    u_host = torch.zeros((3, N), dtype=torch.float64).pin_memory()
+    p_out = torch.empty((N,), dtype=torch.float32).pin_memory()
+    u_out = torch.empty((3, N), dtype=torch.float32).pin_memory()
+    p_dev = torch.empty((N,), dtype=torch.float64, device=device)
+    u_dev = torch.empty((3, N), dtype=torch.float64, device=device)
+    p_o = torch.empty((N,), dtype=torch.float32, device=device)
+    u_o = torch.empty((3, N), dtype=torch.float32, device=device)
+
+    def job(nsteps):
+        p_dev.copy_(p_host, non_blocking=True)
+        u_dev.copy_(u_host, non_blocking=True)
+        lat.init(p_dev, u_dev)
+        for _ in range(nsteps):
+            lat.step(1)
+            lat.reduce()
+        lat.macroscopic_into(p_o, u_o)
+        p_out.copy_(p_o, non_blocking=True)
+        u_out.copy_(u_o, non_blocking=True)
+        torch.cuda.synchronize()
+
+    job(warmup)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    job(steps)
+    barrier(world)
+    dt = max_over_ranks(time.perf_counter() - t0, world, device)
+    h2d = (p_host.numel() + u_host.numel()) * 8
+    d2h = (p_out.numel() + u_out.numel()) * 4
+    res = {"value": world * N * steps / dt / 1e9, "unit": "GLUPS",
+           "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": 48 + d2h / steps,
+           "steps": steps,
+           "what": f"D3Q19 cavity {n}^3 {storage} AA via paper_2201_11330_b300.lbm.Lattice: "
+                   "pinned-host FP64 initial (p, u) -> device, lbm_init, per step lbm_step(1) + "
+                   "lbm_reduce (FP64 monitor to host), final FP32 (p, u) -> pinned host"}
+    del lat
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_adjoint(n, T, K, world, device, warmup=1):
+    """Adjoint/forward time ratio on the periodic box with a Fourier force."""
+    import torch
+    from paper_2201_11330_b300 import workloads as W
+    from paper_2201_11330_b300.lbm import Lattice
+    F = torch.from_numpy(W.fourier_force(n, n, n, amplitude=1e-5, seed=2201)).to(device)
+    lat = Lattice("d3q19", n, n, n, 0.8, "periodic", storage="f32", aa=False, has_force=True)
+    lat.set_force(F)
+    lat.init()
+    lat.step(warmup)
+    lat.init()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.step(T)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    lat.init()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = lat.adjoint_forward(T, K)
+    t_fwd_ck = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g, gU = lat.adjoint_backward()
+    torch.cuda.synchronize()
+    t_bwd = time.perf_counter() - t0
+    res = {"config": f"D3Q19 periodic {n}^3 FP32, Fourier force A=1e-5 seed 2201, T={T}, K={K}",
+           "forward_s": t_fwd, "forward_checkpointed_s": t_fwd_ck, "backward_s": t_bwd,
+           "ratio": t_bwd / t_fwd, "J": J,
+           "ratio_definition": "backward (recompute + adjoint steps) time / plain forward time"}
+    del lat, g
+    torch.cuda.empty_cache()
+    return res
+
+
+def cpu_baseline_sample(target_s=12.0):
+    """The FP64 oracle, as it stands, on this host's cores: D3Q19 cavity at
+    the headline tau on a 96^3 box, enough steps for ~target_s seconds."""
+    import oracle
+    from paper_2201_11330_b300 import workloads as W
+    c = W.cavity_params(HEADLINE["n"], HEADLINE["re"], HEADLINE["lid_u"])
+    n = 96
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.run("d3q19", n, n, n, c["tau"], "cavity", 1, lid=c["lid"], threads=cores)
+    t1 = time.perf_counter() - t0
+    steps = max(2, int(target_s / max(t1, 1e-3)))
+    t0 = time.perf_counter()
+    oracle.run("d3q19", n, n, n, c["tau"], "cavity", steps, lid=c["lid"], threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n ** 3 * steps / dt / 1e9, "unit": "GLUPS", "cores": cores,
+            "kind": "oracle",
+            "sample": f"D3Q19 cavity {n}^3 at the 512^3 workload's tau={c['tau']}, {steps} steps "
+                      f"(init + steps + moments timed), {dt:.1f} s, OpenMP threads={cores}"}
+
+
+# ---------------------------------------------------------------------------
+
+
+def reference_arm(args, world, rank):
+    """Oracle arm: each step is a bounded sample of the headline workload."""
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2201_11330_b300 import workloads as W
+    c = W.cavity_params(HEADLINE["n"], HEADLINE["re"], HEADLINE["lid_u"])
+    n, sub = 64, 2
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.run("d3q19", n, n, n, c["tau"], "cavity", sub, lid=c["lid"], threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run("d3q19", n, n, n, c["tau"], "cavity", sub, lid=c["lid"], threads=cores)
+    dt = time.perf_counter() - t0
+    value = n ** 3 * sub * args.steps / dt / 1e9
+    sample = (f"each step: FP64 oracle D3Q19 cavity {n}^3 at the 512^3 workload's "
+              f"tau={c['tau']}, {sub} time steps incl. init and moments")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(**{k: HEADLINE[k] for k in
+                                                    ("lattice", "n", "re", "storage", "aa")}),
+                       "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--size", type=int, default=HEADLINE["n"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline line only (no storage variants, D3Q27, adjoint, CPU)")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        return reference_arm(args, world, rank)
+
+    import torch
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist_init(world, "nccl")
+    from paper_2201_11330_b300 import build
+    if rank == 0:
+        build.build()
+    barrier(world)
+
+    hb = dict(HEADLINE)
+    hb["n"] = args.size
+    peak, peak_kind = load_peaks()
+
+    # headline, with clocks sampled during its timed region
+    sampler = ClockSampler(local)
+    sampler.start()
+    head = run_cavity(hb["lattice"], hb["n"], hb["re"], hb["storage"], hb["aa"], args.steps,
+                      args.warmup, world, device)
+    clocks = sampler.stop()
+
+    N = head["nodes"]
+    bpn = head["bytes_per_node"]
+    dom_ms = max(head["gather_ms"], head["local_ms"])
+    dom_name = "k_step<D3Q19,F32,GATHER>" if head["gather_ms"] >= head["local_ms"] else \
+        "k_step<D3Q19,F32,LOCAL>"
+    achieved = N * bpn / (dom_ms * 1e-3) / 1e9
+    traffic = load_traffic("d3q19_f32_gather")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": dom_name, "peak_kind": f"{peak_kind} copy bandwidth",
+                "algorithmic_bytes_per_launch": N * bpn,
+                "gather_ms": head["gather_ms"], "local_ms": head["local_ms"],
+                "frac_of_8TBs": N * bpn / (dom_ms * 1e-3) / 8e12}
+
+    extras = {}
+    if not args.no_extras:
+        for st in ("f16s", "bf16s"):
+            r = run_cavity("d3q19", hb["n"], hb["re"], st, True, args.steps, args.warmup, world,
+                           device)
+            r["hbm_frac"] = r["glups"] / world * r["bytes_per_node"] / peak
+            extras[f"d3q19_{st}_aa"] = r
+        r = run_cavity("d3q19", hb["n"], hb["re"], "f32", False, args.steps, args.warmup, world,
+                       device)
+        r["hbm_frac"] = r["glups"] / world * r["bytes_per_node"] / peak
+        extras["d3q19_f32_pull"] = r
+        n27 = 768 if hb["n"] == 512 else hb["n"]
+        r = run_cavity("d3q27", n27, 2000.0, "f16s", True, max(10, args.steps // 4),
+                       args.warmup, world, device)
+        r["hbm_frac"] = r["glups"] / world * r["bytes_per_node"] / peak
+        extras["d3q27_f16s_aa_768"] = r
+        try:
+            extras["adjoint"] = run_adjoint(128, 2000, 100, world, device)
+        except Exception as exc:  # reported, not hidden
+            extras["adjoint"] = {"error": str(exc)}
+    e2e = run_e2e(hb["n"], hb["re"], hb["storage"], max(10, args.steps // 2), args.warmup,
+                  world, device)
+
+    cpu = cpu_baseline_sample() if (rank == 0 and world == 1 and not args.no_extras) else None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": head["glups"], "unit": "GLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": workload_name(hb["lattice"], hb["n"], hb["re"], hb["storage"],
+                                                 hb["aa"]),
+                       "nodes_per_gpu": N, "parallelism": f"replicas x{world}",
+                       "l2": "state larger than L2 (no flush needed)"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "mass_rel_drift": head["mass_rel_drift"],
+        }
+        line.update(extras)
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

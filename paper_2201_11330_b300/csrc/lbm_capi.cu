@@ -1,0 +1,464 @@
+// lbm_capi.cu -- the C ABI declared in include/lbm.h (host side).
+//
+// Owns no device memory: every buffer is carved out of the caller's
+// workspace.  All launches go to the context's stream.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "lbm.h"
+#include "lbm_capi_internal.h"
+#include "lbm_kernels.cuh"
+
+using namespace lbm;
+
+namespace {
+
+constexpr int kMaxReduceBlocks = 1184;  // 8 per SM on 148 SMs
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int lattice_q(int lattice) { return lattice == LBM_D2Q9 ? 9 : lattice == LBM_D3Q19 ? 19 : 27; }
+int lattice_d(int lattice) { return lattice == LBM_D2Q9 ? 2 : 3; }
+size_t storage_elem(int s) { return s == LBM_F64 ? 8 : s == LBM_F32 ? 4 : 2; }
+
+int default_block(int nx)
+{
+    int b = (nx + 31) / 32 * 32;
+    return b > 256 ? 256 : b;
+}
+
+bool valid_shape(int lattice, int nx, int ny, int nz)
+{
+    if (lattice < LBM_D2Q9 || lattice > LBM_D3Q27)
+        return false;
+    if (nx < 1 || ny < 1 || nz < 1 || ny > 65535 || nz > 65535)
+        return false;
+    if (lattice == LBM_D2Q9 && nz != 1)
+        return false;
+    const long long N = (long long)nx * ny * nz;
+    return N < (1LL << 31);
+}
+
+bool valid_opts(const lbm_opts &o)
+{
+    if (o.storage < LBM_F64 || o.storage > LBM_BF16S)
+        return false;
+    if (!(o.rho0 > 0.0) || !isfinite(o.rho0))
+        return false;
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(o.lid_u[k]))
+            return false;
+    return true;
+}
+
+struct Layout {
+    size_t state_bytes, f_off[2], partial_off, result_off, total;
+    int nred;
+};
+
+Layout layout_for(int lattice, int nx, int ny, int nz, const lbm_opts &o)
+{
+    Layout L;
+    const size_t N = (size_t)nx * ny * nz;
+    L.state_bytes = (size_t)lattice_q(lattice) * N * storage_elem(o.storage);
+    size_t off = 0;
+    L.f_off[0] = off;
+    off += align_up(L.state_bytes);
+    L.f_off[1] = off;
+    if (!o.aa)
+        off += align_up(L.state_bytes);
+    const int bx = default_block(nx);
+    const long long nseg = (long long)((nx + bx - 1) / bx) * ny * nz;
+    L.nred = (int)(nseg < kMaxReduceBlocks ? nseg : kMaxReduceBlocks);
+    L.partial_off = off;
+    off += align_up((size_t)L.nred * kPartialStride * sizeof(double));
+    L.result_off = off;
+    off += kAlign;
+    L.total = off;
+    return L;
+}
+
+cudaError_t dispatch(int lattice, const Launch &l)
+{
+    switch (lattice) {
+    case LBM_D2Q9:
+        return launch_d2q9(l);
+    case LBM_D3Q19:
+        return launch_d3q19(l);
+    default:
+        return launch_d3q27(l);
+    }
+}
+
+template <class L>
+void fill_lid_terms(lbm_ctx *c)
+{
+    for (int a = 0; a < L::Q; ++a) {
+        const double eU = L::e(a, 0) * c->opts.lid_u[0] + L::e(a, 1) * c->opts.lid_u[1] +
+                          L::e(a, 2) * c->opts.lid_u[2];
+        const double v = 2.0 * L::w(a) * c->opts.rho0 * eU * 3.0;
+        c->sp.cd.lid[a] = v;
+        c->sp.cf.lid[a] = (float)v;
+    }
+}
+
+void fill_params(lbm_ctx *c)
+{
+    StepParams &p = c->sp;
+    p.nx = c->nx;
+    p.ny = c->ny;
+    p.nz = c->nz;
+    p.N = (int)c->N;
+    p.periodic = c->bc == LBM_BC_PERIODIC ? 7 : c->bc == LBM_BC_CHANNEL ? 5 : 0;
+    p.lid_on = c->bc != LBM_BC_PERIODIC;
+    const double omega = 1.0 / c->tau;
+    const double sigma = c->shifted ? 1.0 : 0.0;
+    p.cd.omega = omega;
+    p.cd.rho0 = c->opts.rho0;
+    p.cd.inv_rho0 = 1.0 / c->opts.rho0;
+    p.cd.sigma = sigma;
+    p.cd.kf = (1.0 - 0.5 * omega) / omega;
+    p.cf.omega = (float)omega;
+    p.cf.rho0 = (float)c->opts.rho0;
+    p.cf.inv_rho0 = (float)(1.0 / c->opts.rho0);
+    p.cf.sigma = (float)sigma;
+    p.cf.kf = (float)p.cd.kf;
+    for (int a = 0; a < kMaxQ; ++a) {
+        p.cd.lid[a] = 0.0;
+        p.cf.lid[a] = 0.0f;
+    }
+    if (c->lattice == LBM_D2Q9)
+        fill_lid_terms<D2Q9>(c);
+    else if (c->lattice == LBM_D3Q19)
+        fill_lid_terms<D3Q19>(c);
+    else
+        fill_lid_terms<D3Q27>(c);
+    p.F = c->force;
+    p.u_out = nullptr;
+}
+
+Launch base_launch(const lbm_ctx *c, int kind)
+{
+    Launch l;
+    memset(&l, 0, sizeof(l));
+    l.kind = kind;
+    l.storage = c->opts.storage;
+    l.comp = c->opts.compressible != 0;
+    l.force = c->force != nullptr;
+    l.uout = false;
+    l.sp = c->sp;
+    l.block = dim3(c->bx, 1, 1);
+    l.grid = dim3((c->nx + c->bx - 1) / c->bx, c->ny, c->nz);
+    l.stream = c->stream;
+    return l;
+}
+
+}  // namespace
+
+// ---- internal helpers shared with the adjoint driver ------------------------
+namespace lbm {
+
+int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, float *u_out)
+{
+    Launch l = base_launch(c, K_STEP);
+    l.pattern = pattern;
+    l.src = src;
+    l.dst = dst;
+    if (u_out) {
+        l.uout = true;
+        l.sp.u_out = u_out;
+    }
+    return dispatch(c->lattice, l) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+int ctx_launch_moments(lbm_ctx *c, const void *src, int form, void *p_out, void *u_out,
+                       int out_f32, double *partials)
+{
+    Launch l = base_launch(c, K_MOMENTS);
+    l.pattern = form;
+    l.src = src;
+    l.mp.p_out = p_out;
+    l.mp.u_out = u_out;
+    l.mp.out_f32 = out_f32;
+    l.mp.partials = partials;
+    l.mp.xseg = (c->nx + c->bx - 1) / c->bx;
+    l.mp.nseg = l.mp.xseg * c->ny * c->nz;
+    l.grid = dim3(c->nred, 1, 1);
+    return dispatch(c->lattice, l) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+int ctx_current_form(const lbm_ctx *c)
+{
+    if (!c->opts.aa)
+        return FORM_LOCAL;
+    return (c->step % 2 == 0) ? FORM_SWAPPED : FORM_STREAMED;
+}
+
+const void *ctx_state(const lbm_ctx *c) { return c->opts.aa ? c->f[0] : c->f[c->cur]; }
+
+}  // namespace lbm
+
+// ---- C ABI -------------------------------------------------------------------
+extern "C" {
+
+void lbm_default_opts(lbm_opts *o)
+{
+    if (!o)
+        return;
+    memset(o, 0, sizeof(*o));
+    o->storage = LBM_F32;
+    o->rho0 = 1.0;
+}
+
+double lbm_tau_from_paper(double tau_paper) { return tau_paper + 0.5; }
+
+size_t lbm_workspace_bytes(int lattice, int nx, int ny, int nz, const lbm_opts *opts)
+{
+    lbm_opts o;
+    if (opts)
+        o = *opts;
+    else
+        lbm_default_opts(&o);
+    if (!valid_shape(lattice, nx, ny, nz) || !valid_opts(o))
+        return 0;
+    return layout_for(lattice, nx, ny, nz, o).total;
+}
+
+int lbm_create(int lattice, int nx, int ny, int nz, double tau, int bc, const lbm_opts *opts,
+               void *dev_workspace, size_t bytes, void *cuda_stream, lbm_ctx **out)
+{
+    if (!out)
+        return LBM_ERR_ARG;
+    *out = nullptr;
+    lbm_opts o;
+    if (opts)
+        o = *opts;
+    else
+        lbm_default_opts(&o);
+    if (!valid_shape(lattice, nx, ny, nz) || !valid_opts(o))
+        return LBM_ERR_ARG;
+    if (!(tau > 0.5) || !isfinite(tau))
+        return LBM_ERR_ARG;
+    if (bc < LBM_BC_PERIODIC || bc > LBM_BC_CHANNEL)
+        return LBM_ERR_ARG;
+    if (!dev_workspace || ((uintptr_t)dev_workspace % kAlign) != 0)
+        return LBM_ERR_ARG;
+    const Layout L = layout_for(lattice, nx, ny, nz, o);
+    if (bytes < L.total)
+        return LBM_ERR_NOMEM;
+    lbm_ctx *c = new (std::nothrow) lbm_ctx;
+    if (!c)
+        return LBM_ERR_NOMEM;
+    memset(c, 0, sizeof(*c));
+    c->lattice = lattice;
+    c->Q = lattice_q(lattice);
+    c->d = lattice_d(lattice);
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->N = (int64_t)nx * ny * nz;
+    c->tau = tau;
+    c->bc = bc;
+    c->opts = o;
+    if (bc == LBM_BC_PERIODIC)
+        for (int k = 0; k < 3; ++k)
+            c->opts.lid_u[k] = 0.0;
+    c->shifted = o.storage != LBM_F64 && !(o.storage == LBM_F32 && o.f32_unshifted);
+    c->ws = (char *)dev_workspace;
+    c->ws_bytes = bytes;
+    c->state_bytes = L.state_bytes;
+    c->f[0] = c->ws + L.f_off[0];
+    c->f[1] = o.aa ? c->f[0] : c->ws + L.f_off[1];
+    c->cur = 0;
+    c->nred = L.nred;
+    c->partials = (double *)(c->ws + L.partial_off);
+    c->result = (double *)(c->ws + L.result_off);
+    c->stream = (cudaStream_t)cuda_stream;
+    c->force = nullptr;
+    c->step = 0;
+    c->bx = default_block(nx);
+    c->initialized = false;
+    fill_params(c);
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_set_stream(lbm_ctx *c, void *cuda_stream)
+{
+    if (!c)
+        return LBM_ERR_ARG;
+    c->stream = (cudaStream_t)cuda_stream;
+    return LBM_OK;
+}
+
+int lbm_init(lbm_ctx *c, const double *p, const double *u)
+{
+    if (!c)
+        return LBM_ERR_ARG;
+    Launch l = base_launch(c, K_INIT);
+    l.pattern = c->opts.aa ? 1 : 0;
+    l.p0 = p;
+    l.u0 = u;
+    c->cur = 0;
+    l.dst = c->f[0];
+    c->step = 0;
+    if (dispatch(c->lattice, l) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    c->initialized = true;
+    return LBM_OK;
+}
+
+int lbm_set_force(lbm_ctx *c, const float *force)
+{
+    if (!c)
+        return LBM_ERR_ARG;
+    if (!c->opts.has_force)
+        return LBM_ERR_STATE;
+    c->force = force;
+    c->sp.F = force;
+    return LBM_OK;
+}
+
+int lbm_set_lid(lbm_ctx *c, const double *lid_u3)
+{
+    if (!c || !lid_u3)
+        return LBM_ERR_ARG;
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(lid_u3[k]))
+            return LBM_ERR_ARG;
+    if (c->bc == LBM_BC_PERIODIC)
+        return LBM_OK;
+    for (int k = 0; k < 3; ++k)
+        c->opts.lid_u[k] = lid_u3[k];
+    fill_params(c);
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx *c, int64_t n)
+{
+    if (!c || n < 0)
+        return LBM_ERR_ARG;
+    if (!c->initialized)
+        return LBM_ERR_STATE;
+    for (int64_t i = 0; i < n; ++i) {
+        int rc;
+        if (c->opts.aa) {
+            const int pat = (c->step % 2 == 0) ? PAT_GATHER : PAT_LOCAL;
+            rc = ctx_launch_step(c, c->f[0], c->f[0], pat, nullptr);
+        } else {
+            rc = ctx_launch_step(c, c->f[c->cur], c->f[1 - c->cur], PAT_PULL, nullptr);
+            if (rc == LBM_OK)
+                c->cur = 1 - c->cur;
+        }
+        if (rc != LBM_OK)
+            return rc;
+        ++c->step;
+    }
+    return LBM_OK;
+}
+
+int64_t lbm_step_count(const lbm_ctx *c) { return c ? c->step : -1; }
+
+int lbm_macroscopic(lbm_ctx *c, void *p_out, void *u_out, int out_dtype)
+{
+    if (!c || (out_dtype != 0 && out_dtype != 1))
+        return LBM_ERR_ARG;
+    if (!c->initialized)
+        return LBM_ERR_STATE;
+    if (!p_out && !u_out)
+        return LBM_OK;
+    return ctx_launch_moments(c, ctx_state(c), ctx_current_form(c), p_out, u_out, out_dtype,
+                              nullptr);
+}
+
+int lbm_reduce(lbm_ctx *c, double *out)
+{
+    if (!c || !out)
+        return LBM_ERR_ARG;
+    if (!c->initialized)
+        return LBM_ERR_STATE;
+    int rc = ctx_launch_moments(c, ctx_state(c), ctx_current_form(c), nullptr, nullptr, 0,
+                                c->partials);
+    if (rc != LBM_OK)
+        return rc;
+    if (launch_finish(c->partials, c->nred, c->result, c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    double r[kReduceVals];
+    if (cudaMemcpyAsync(r, c->result, sizeof(r), cudaMemcpyDeviceToHost, c->stream) !=
+        cudaSuccess)
+        return LBM_ERR_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    out[0] = r[0] + (c->shifted ? (double)c->N : 0.0);
+    out[1] = r[1];
+    out[2] = r[2];
+    out[3] = r[3];
+    out[4] = r[4];
+    out[5] = sqrt(r[5]);
+    for (int k = 0; k < kReduceVals; ++k)
+        if (!isfinite(out[k]))
+            return LBM_ERR_UNSTABLE;
+    return LBM_OK;
+}
+
+size_t lbm_state_bytes(const lbm_ctx *c) { return c ? c->state_bytes : 0; }
+
+int lbm_get_state(lbm_ctx *c, void *dst, int64_t *step)
+{
+    if (!c || !dst)
+        return LBM_ERR_ARG;
+    if (!c->initialized)
+        return LBM_ERR_STATE;
+    if (cudaMemcpyAsync(dst, ctx_state(c), c->state_bytes, cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    if (step)
+        *step = c->step;
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_ctx *c, const void *src, int64_t step)
+{
+    if (!c || !src || step < 0)
+        return LBM_ERR_ARG;
+    if (cudaMemcpyAsync((void *)ctx_state(c), src, c->state_bytes, cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    c->step = step;
+    c->initialized = true;
+    return LBM_OK;
+}
+
+const char *lbm_error_string(int status)
+{
+    switch (status) {
+    case LBM_OK:
+        return "ok";
+    case LBM_ERR_ARG:
+        return "invalid argument";
+    case LBM_ERR_CUDA:
+        return "CUDA launch or copy failed";
+    case LBM_ERR_UNSTABLE:
+        return "non-finite value in the state (unstable run)";
+    case LBM_ERR_STATE:
+        return "call not valid in the current state";
+    case LBM_ERR_NOMEM:
+        return "workspace too small";
+    }
+    return "unknown status";
+}
+
+void lbm_destroy(lbm_ctx *c) { delete c; }
+
+}  // extern "C"
+
+namespace lbm {
+cudaError_t launch_finish(const double *partials, int nblocks, double *out, cudaStream_t s)
+{
+    k_reduce_finish<<<1, 256, 0, s>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+}  // namespace lbm

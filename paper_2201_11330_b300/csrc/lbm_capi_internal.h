@@ -1,0 +1,41 @@
+// lbm_capi_internal.h -- the context object and helpers shared by the host
+// translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm.h"
+#include "lbm_kernels.cuh"
+
+struct lbm_ctx {
+    int lattice, Q, d;
+    int nx, ny, nz;
+    int64_t N;
+    double tau;
+    int bc;
+    lbm_opts opts;
+    bool shifted;
+    char *ws;
+    size_t ws_bytes;
+    void *f[2];  // pull scheme: current state f[cur]; AA: f[0] only
+    int cur;
+    size_t state_bytes;
+    int nred;  // moment-kernel blocks (reduction partials)
+    double *partials;
+    double *result;
+    cudaStream_t stream;
+    const float *force;
+    int64_t step;
+    int bx;  // threads per block along x
+    bool initialized;
+    lbm::StepParams sp;
+};
+
+namespace lbm {
+int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, float *u_out);
+int ctx_launch_moments(lbm_ctx *c, const void *src, int form, void *p_out, void *u_out,
+                       int out_f32, double *partials);
+int ctx_current_form(const lbm_ctx *c);
+const void *ctx_state(const lbm_ctx *c);
+}  // namespace lbm

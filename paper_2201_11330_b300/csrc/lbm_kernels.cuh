@@ -1,0 +1,724 @@
+// lbm_kernels.cuh -- fused stream-collide, initialisation and moment kernels.
+//
+// One launch of k_step is one IMEXLBM time step (arxiv 2201.11330, Sec. 3.1:
+// Collision -> BoundaryCondition -> Propagation -> PostProcessing), fused:
+// each thread owns one node, gathers its Q incoming populations (propagation,
+// Eq. (propagation), with half-way bounce-back, Eq. (bb), and the moving-lid
+// term at walls, index wrap at periodic faces), takes the moments (Sec. 2.1),
+// relaxes towards the incompressible equilibrium of Eq. (incompressible_feq)
+// (or Eq. (feq)) with the IMEX factor omega = 1/(tau_paper + 1/2) of Eq.
+// (collision), and stores the post-collision populations.  The stored state
+// is therefore always post-collision; moments are computed from it on demand.
+//
+// Layout in HBM: structure of arrays, slot a of node n at f[a*N + n], node
+// index n = x + nx*(y + ny*z), x fastest.  Three access patterns:
+//   PAT_PULL   two lattices: read slot a of the upstream node x - e_a from
+//              `src`, write slot a of x to `dst`.
+//   PAT_GATHER single lattice (AA pattern, first half): read slot abar of
+//              x - e_a, write slot a of x + e_a (in place).
+//   PAT_LOCAL  single lattice (AA pattern, second half): read slot a of x,
+//              write slot abar of x (in place).
+// A thread of PAT_GATHER reads exactly the locations it writes, so the
+// in-place update is race-free without synchronisation.
+#pragma once
+
+#include "lbm_lattice.cuh"
+
+namespace lbm {
+
+enum Pattern { PAT_PULL = 0, PAT_GATHER = 1, PAT_LOCAL = 2 };
+// Where post-collision populations f*_a(x) sit in the stored state.
+enum Form { FORM_LOCAL = 0, FORM_SWAPPED = 1, FORM_STREAMED = 2 };
+
+constexpr int kMaxQ = 27;
+constexpr int kReduceVals = 6;  // sum dP, momentum x/y/z, kinetic energy, max |u|^2
+constexpr int kPartialStride = 8;
+
+template <class R>
+struct Coef {
+    R omega;     // 1/tau (standard tau)
+    R rho0;      // constant density of the incompressible model
+    R inv_rho0;  // 1/rho0
+    R sigma;     // 1 when the storage holds f - t, else 0
+    R kf;        // (1 - omega/2)/omega: force source folded into the equilibrium
+    R lid[kMaxQ];  // 2 t_a rho0 (e_a . U)/c_s^2 for links crossing the moving wall
+};
+
+struct StepParams {
+    int nx, ny, nz;
+    int N;
+    int periodic;  // bit k set: axis k is periodic, else walled
+    int lid_on;    // the +y wall moves
+    Coef<float> cf;
+    Coef<double> cd;
+    const float *F;  // body force, d*N component-major (FORCE kernels)
+    float *u_out;    // velocity output, d*N component-major (UOUT kernels)
+};
+
+template <class R>
+__device__ __forceinline__ const Coef<R> &coef(const StepParams &p);
+template <>
+__device__ __forceinline__ const Coef<float> &coef<float>(const StepParams &p)
+{
+    return p.cf;
+}
+template <>
+__device__ __forceinline__ const Coef<double> &coef<double>(const StepParams &p)
+{
+    return p.cd;
+}
+
+// ---- memory access ---------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T ld(const T *p)
+{
+#ifdef LBM_STREAMING_HINTS
+    return __ldcs(p);
+#else
+    return *p;
+#endif
+}
+template <class T>
+__device__ __forceinline__ void st(T *p, T v)
+{
+#ifdef LBM_STREAMING_HINTS
+    __stcs(p, v);
+#else
+    *p = v;
+#endif
+}
+
+// ---- collision (Sec. 2.1) ---------------------------------------------------
+// g holds the populations (shifted by sigma*t_a when the storage is shifted);
+// on return it holds the post-collision populations in the same shift.  The
+// incompressible update is invariant under that shift, so only the
+// compressible density rho = sum g + sigma sees it.  u returns the velocity
+// (j + F/2)/rho.  The Guo source (1 - omega/2) S_a is folded into the
+// equilibrium as kf*S_a, and opposite directions are handled in pairs:
+//   feq_a = t_a [A + 4.5 rho (e.u)^2] +/- t_a 3 rho (e.u),
+//   A = sum g - 1.5 rho u.u  (the sigma*t_a shift cancels).
+template <class L, class R, bool COMP, bool FORCE>
+__device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coef<R> &c,
+                                        R (&u)[3])
+{
+    constexpr int H = L::Q / 2;
+    R sp[H], sm[H];
+    SFor<0, H>::run([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        sp[a] = g[a] + g[opp<L>(a)];
+        sm[a] = g[a] - g[opp<L>(a)];
+    });
+    R s = g[H];
+    R j[3] = {R(0), R(0), R(0)};
+    SFor<0, H>::run([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        s += sp[a];
+        SFor<0, 3>::run([&](auto K_) {
+            constexpr int k = decltype(K_)::value;
+            if constexpr (L::e(a, k) == 1)
+                j[k] += sm[a];
+            else if constexpr (L::e(a, k) == -1)
+                j[k] -= sm[a];
+        });
+    });
+    R rho, ir;
+    if constexpr (COMP) {
+        rho = s + c.sigma;
+        ir = R(1) / rho;
+    } else {
+        rho = c.rho0;
+        ir = c.inv_rho0;
+    }
+    SFor<0, 3>::run([&](auto K_) {
+        constexpr int k = decltype(K_)::value;
+        if constexpr (FORCE)
+            u[k] = (j[k] + R(0.5) * F[k]) * ir;
+        else
+            u[k] = j[k] * ir;
+    });
+    const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    R A = s - R(1.5) * rho * uu;
+    R uF = R(0);
+    if constexpr (FORCE) {
+        uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+        A -= R(3) * c.kf * uF;
+    }
+    const R r3 = R(3) * rho, r45 = R(4.5) * rho;
+    const R om = c.omega;
+    SFor<0, H>::run([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        constexpr int b = opp<L>(a);
+        const R t = R(L::w(a));
+        R eu = R(0), eF = R(0);
+        (void)eF;
+        SFor<0, 3>::run([&](auto K_) {
+            constexpr int k = decltype(K_)::value;
+            if constexpr (L::e(a, k) == 1) {
+                eu += u[k];
+                if constexpr (FORCE)
+                    eF += F[k];
+            } else if constexpr (L::e(a, k) == -1) {
+                eu -= u[k];
+                if constexpr (FORCE)
+                    eF -= F[k];
+            }
+        });
+        R sym = A + r45 * eu * eu;
+        R asym = r3 * eu;
+        if constexpr (FORCE) {
+            sym += R(9) * c.kf * eu * eF;
+            asym += R(3) * c.kf * eF;
+        }
+        sym *= t;
+        asym *= t;
+        const R fa = sym + asym, fb = sym - asym;
+        g[a] = g[a] + om * (fa - g[a]);
+        g[b] = g[b] + om * (fb - g[b]);
+    });
+    {
+        const R t0 = R(L::w(H));
+        g[H] = g[H] + om * (t0 * A - g[H]);
+    }
+}
+
+// ---- neighbours -------------------------------------------------------------
+// For one axis at coordinate c: node offsets of the upstream node along -e
+// for e = +1 (upstream c-1, `op`) and e = -1 (upstream c+1, `om`), and
+// whether that upstream node lies beyond a wall.
+struct AxisNbr {
+    int op, om;
+    bool wp, wm;
+};
+
+__device__ __forceinline__ AxisNbr axis_general(int c, int n, int stride, bool periodic)
+{
+    AxisNbr a;
+    a.wp = false;
+    a.wm = false;
+    if (c > 0) {
+        a.op = -stride;
+    } else {
+        a.op = periodic ? (n - 1) * stride : 0;
+        a.wp = !periodic;
+    }
+    if (c < n - 1) {
+        a.om = stride;
+    } else {
+        a.om = periodic ? -(n - 1) * stride : 0;
+        a.wm = !periodic;
+    }
+    return a;
+}
+
+__device__ __forceinline__ AxisNbr axis_interior(int stride)
+{
+    AxisNbr a;
+    a.op = -stride;
+    a.om = stride;
+    a.wp = false;
+    a.wm = false;
+    return a;
+}
+
+// Upstream offset and wall flag of direction a (pull source x - e_a).
+template <class L, int a>
+__device__ __forceinline__ void upstream(const AxisNbr &X, const AxisNbr &Y, const AxisNbr &Z,
+                                         int &off, bool &wall)
+{
+    constexpr int ex = L::e(a, 0), ey = L::e(a, 1), ez = L::e(a, 2);
+    off = 0;
+    wall = false;
+    if constexpr (ex == 1) {
+        off += X.op;
+        wall = wall || X.wp;
+    } else if constexpr (ex == -1) {
+        off += X.om;
+        wall = wall || X.wm;
+    }
+    if constexpr (ey == 1) {
+        off += Y.op;
+        wall = wall || Y.wp;
+    } else if constexpr (ey == -1) {
+        off += Y.om;
+        wall = wall || Y.wm;
+    }
+    if constexpr (ez == 1) {
+        off += Z.op;
+        wall = wall || Z.wp;
+    } else if constexpr (ez == -1) {
+        off += Z.om;
+        wall = wall || Z.wm;
+    }
+}
+
+template <class L, bool INTERIOR>
+__device__ __forceinline__ void make_axes(const StepParams &p, int x, int y, int z, AxisNbr &X,
+                                          AxisNbr &Y, AxisNbr &Z)
+{
+    X = axis_general(x, p.nx, 1, p.periodic & 1);
+    if constexpr (INTERIOR) {
+        Y = axis_interior(p.nx);
+        Z = axis_interior(p.nx * p.ny);
+    } else {
+        Y = axis_general(y, p.ny, p.nx, p.periodic & 2);
+        if constexpr (L::D == 3)
+            Z = axis_general(z, p.nz, p.nx * p.ny, p.periodic & 4);
+        else
+            Z = axis_interior(0);
+    }
+}
+
+// ---- one node of one time step ----------------------------------------------
+template <class L, int S, int PAT, bool COMP, bool FORCE, bool UOUT, bool INTERIOR>
+__device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typename Sto<S>::T *dst,
+                                          const StepParams &p, int x, int y, int z)
+{
+    using T = typename Sto<S>::T;
+    using R = typename Sto<S>::R;
+    constexpr int Q = L::Q;
+    const Coef<R> &c = coef<R>(p);
+    const size_t N = (size_t)p.N;
+    const int n = x + p.nx * (y + p.ny * z);
+    AxisNbr X, Y, Z;
+    make_axes<L, INTERIOR>(p, x, y, z, X, Y, Z);
+    const bool lid_row = !INTERIOR && p.lid_on && (y == p.ny - 1);
+
+    R g[Q];
+    if constexpr (PAT == PAT_LOCAL) {
+        SFor<0, Q>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            g[a] = Sto<S>::dec(ld(src + a * N + n));
+        });
+    } else {
+        SFor<0, Q>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            constexpr int b = opp<L>(a);
+            int off;
+            bool wall;
+            upstream<L, a>(X, Y, Z, off, wall);
+            const T *ptr;
+            if constexpr (PAT == PAT_PULL)
+                ptr = wall ? src + b * N + n : src + a * N + (n + off);
+            else
+                ptr = wall ? src + a * N + n : src + b * N + (n + off);
+            R v = Sto<S>::dec(ld(ptr));
+            if constexpr (L::e(a, 1) == -1) {
+                if (lid_row)
+                    v += c.lid[a];
+            }
+            g[a] = v;
+        });
+    }
+    R F[3] = {R(0), R(0), R(0)};
+    if constexpr (FORCE) {
+        SFor<0, L::D>::run([&](auto K_) {
+            constexpr int k = decltype(K_)::value;
+            F[k] = R(p.F[k * N + n]);
+        });
+    }
+    R u[3];
+    collide<L, R, COMP, FORCE>(g, F, c, u);
+    if constexpr (UOUT) {
+        SFor<0, L::D>::run([&](auto K_) {
+            constexpr int k = decltype(K_)::value;
+            p.u_out[k * N + n] = float(u[k]);
+        });
+    }
+    SFor<0, Q>::run([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        constexpr int b = opp<L>(a);
+        if constexpr (PAT == PAT_PULL) {
+            st(dst + a * N + n, Sto<S>::enc(g[a]));
+        } else if constexpr (PAT == PAT_LOCAL) {
+            st(dst + b * N + n, Sto<S>::enc(g[a]));
+        } else {
+            // push f*_a to x + e_a, whose upstream along -e_b is x
+            int off;
+            bool wall;
+            upstream<L, b>(X, Y, Z, off, wall);
+            if (wall) {
+                R v = g[a];
+                if constexpr (L::e(b, 1) == -1) {
+                    if (lid_row)
+                        v += c.lid[b];
+                }
+                st(dst + b * N + n, Sto<S>::enc(v));
+            } else {
+                st(dst + a * N + (n + off), Sto<S>::enc(g[a]));
+            }
+        }
+    });
+}
+
+// grid: (ceil(nx/blockDim.x), ny, nz); one node per thread.
+template <class L, int S, int PAT, bool COMP, bool FORCE, bool UOUT>
+__global__ void __launch_bounds__(256) k_step(const typename Sto<S>::T *src,
+                                              typename Sto<S>::T *dst, const StepParams p)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= p.nx)
+        return;
+    if constexpr (PAT == PAT_LOCAL) {
+        step_node<L, S, PAT, COMP, FORCE, UOUT, true>(src, dst, p, x, y, z);
+    } else {
+        const bool interior =
+            y > 0 && y < p.ny - 1 && (L::D == 2 || (z > 0 && z < p.nz - 1));
+        if (interior)
+            step_node<L, S, PAT, COMP, FORCE, UOUT, true>(src, dst, p, x, y, z);
+        else
+            step_node<L, S, PAT, COMP, FORCE, UOUT, false>(src, dst, p, x, y, z);
+    }
+}
+
+// ---- initialisation (Sec. 2.2: f = feq(p, u), then the first collision) -----
+struct InitParams {
+    const double *p0;  // N or NULL (p = 1/3)
+    const double *u0;  // d*N or NULL (u = 0)
+    int compressible_unused;
+};
+
+template <class L, int S, bool AA, bool COMP, bool FORCE>
+__global__ void __launch_bounds__(256) k_init(typename Sto<S>::T *dst, const StepParams p,
+                                              const double *p0, const double *u0)
+{
+    constexpr int Q = L::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= p.nx)
+        return;
+    const size_t N = (size_t)p.N;
+    const int n = x + p.nx * (y + p.ny * z);
+    const Coef<double> &c = p.cd;
+    const double P = p0 ? 3.0 * p0[n] : 1.0;
+    double u[3] = {0.0, 0.0, 0.0};
+    if (u0)
+        for (int k = 0; k < L::D; ++k)
+            u[k] = u0[k * N + n];
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double g[Q];
+    SFor<0, Q>::run([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        const double t = L::w(a);
+        const double eu = L::e(a, 0) * u[0] + L::e(a, 1) * u[1] + L::e(a, 2) * u[2];
+        const double poly = 3.0 * eu + 4.5 * eu * eu - 1.5 * uu;
+        const double feq = COMP ? t * P * (1.0 + poly) : t * (P + c.rho0 * poly);
+        g[a] = feq - c.sigma * t;
+    });
+    if constexpr (FORCE) {
+        double F[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < L::D; ++k)
+            F[k] = p.F[k * N + n];
+        double uc[3];
+        collide<L, double, COMP, true>(g, F, c, uc);
+    }
+    SFor<0, Q>::run([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        using R = typename Sto<S>::R;
+        const int slot = AA ? opp<L>(a) : a;
+        dst[slot * N + n] = Sto<S>::enc(R(g[a]));
+    });
+}
+
+// ---- moments + FP64 reduction (Sec. 3.4 PostProcessing and Monitor) ---------
+struct MomParams {
+    void *p_out;  // N values or NULL
+    void *u_out;  // d*N values or NULL
+    int out_f32;
+    double *partials;  // gridDim.x * kPartialStride doubles, or NULL
+    int nseg;          // x-segments * ny * nz
+    int xseg;          // x-segments per row
+};
+
+template <class R>
+__device__ __forceinline__ R warp_sum(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <class R>
+__device__ __forceinline__ R warp_max(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Grid-stride over x-segments of rows; each block keeps FP64 partial sums of
+// the per-node values (reduced across a warp in the kernel's arithmetic
+// first) and writes them to partials[blockIdx.x].
+template <class L, int S, int FORM, bool COMP, bool FORCE>
+__global__ void __launch_bounds__(256) k_moments(const typename Sto<S>::T *src, const StepParams p,
+                                                 const MomParams m)
+{
+    using T = typename Sto<S>::T;
+    using R = typename Sto<S>::R;
+    constexpr int Q = L::Q;
+    const Coef<R> &c = coef<R>(p);
+    const size_t N = (size_t)p.N;
+    double acc[kReduceVals] = {0, 0, 0, 0, 0, 0};
+    const int lane = threadIdx.x & 31;
+    for (int seg = blockIdx.x; seg < m.nseg; seg += gridDim.x) {
+        const int xs = seg % m.xseg;
+        const int row = seg / m.xseg;
+        const int y = row % p.ny, z = row / p.ny;
+        const int x = xs * blockDim.x + threadIdx.x;
+        R vals[kReduceVals] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+        if (x < p.nx) {
+            const int n = x + p.nx * (y + p.ny * z);
+            R g[Q];
+            if constexpr (FORM == FORM_LOCAL) {
+                SFor<0, Q>::run([&](auto A_) {
+                    constexpr int a = decltype(A_)::value;
+                    g[a] = Sto<S>::dec(src[a * N + n]);
+                });
+            } else if constexpr (FORM == FORM_SWAPPED) {
+                SFor<0, Q>::run([&](auto A_) {
+                    constexpr int a = decltype(A_)::value;
+                    g[a] = Sto<S>::dec(src[opp<L>(a) * N + n]);
+                });
+            } else {
+                AxisNbr X, Y, Z;
+                make_axes<L, false>(p, x, y, z, X, Y, Z);
+                const bool lid_row = p.lid_on && (y == p.ny - 1);
+                SFor<0, Q>::run([&](auto A_) {
+                    constexpr int a = decltype(A_)::value;
+                    constexpr int b = opp<L>(a);
+                    int off;
+                    bool wall;
+                    upstream<L, b>(X, Y, Z, off, wall);
+                    if (wall) {
+                        R v = Sto<S>::dec(src[b * N + n]);
+                        if constexpr (L::e(b, 1) == -1) {
+                            if (lid_row)
+                                v -= c.lid[b];
+                        }
+                        g[a] = v;
+                    } else {
+                        g[a] = Sto<S>::dec(src[a * N + (n + off)]);
+                    }
+                });
+            }
+            R s = R(0), j[3] = {R(0), R(0), R(0)};
+            SFor<0, Q>::run([&](auto A_) {
+                constexpr int a = decltype(A_)::value;
+                s += g[a];
+                SFor<0, 3>::run([&](auto K_) {
+                    constexpr int k = decltype(K_)::value;
+                    if constexpr (L::e(a, k) == 1)
+                        j[k] += g[a];
+                    else if constexpr (L::e(a, k) == -1)
+                        j[k] -= g[a];
+                });
+            });
+            // post-collision state: j* = j + F, so u = (j* - F/2)/rho
+            const R rho = COMP ? s + c.sigma : c.rho0;
+            const R ir = COMP ? R(1) / rho : c.inv_rho0;
+            R u[3];
+            for (int k = 0; k < 3; ++k) {
+                R jk = j[k];
+                if constexpr (FORCE) {
+                    if (k < L::D)
+                        jk -= R(0.5) * R(p.F[k * N + n]);
+                }
+                u[k] = jk * ir;
+            }
+            const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            if (m.p_out) {
+                const R pv = (s + c.sigma) * R(1.0 / 3.0);
+                if (m.out_f32)
+                    ((float *)m.p_out)[n] = float(pv);
+                else
+                    ((double *)m.p_out)[n] = double(pv);
+            }
+            if (m.u_out) {
+                for (int k = 0; k < L::D; ++k) {
+                    if (m.out_f32)
+                        ((float *)m.u_out)[k * N + n] = float(u[k]);
+                    else
+                        ((double *)m.u_out)[k * N + n] = double(u[k]);
+                }
+            }
+            vals[0] = s;
+            vals[1] = rho * u[0];
+            vals[2] = rho * u[1];
+            vals[3] = rho * u[2];
+            vals[4] = R(0.5) * rho * uu;
+            vals[5] = uu;
+        }
+        if (m.partials) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const R w = warp_sum(vals[k]);
+                if (lane == 0)
+                    acc[k] += double(w);
+            }
+            const R mx = warp_max(vals[5]);
+            if (lane == 0)
+                acc[5] = fmax(acc[5], double(mx));
+        }
+    }
+    if (!m.partials)
+        return;
+    __shared__ double sh[8][kReduceVals];
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < kReduceVals; ++k)
+            sh[warp][k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x < kReduceVals) {
+        const int k = threadIdx.x;
+        double r = sh[0][k];
+        for (int w = 1; w < nwarps; ++w)
+            r = (k == 5) ? fmax(r, sh[w][k]) : r + sh[w][k];
+        m.partials[blockIdx.x * kPartialStride + k] = r;
+    }
+}
+
+// One block: fixed-order sum of the per-block partials into out[0..5].
+static __global__ void __launch_bounds__(256) k_reduce_finish(const double *partials, int nblocks,
+                                                       double *out)
+{
+    __shared__ double sh[256][kReduceVals];
+    double acc[kReduceVals] = {0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int k = 0; k < kReduceVals; ++k)
+            acc[k] = (k == 5) ? fmax(acc[k], partials[b * kPartialStride + k])
+                              : acc[k] + partials[b * kPartialStride + k];
+    for (int k = 0; k < kReduceVals; ++k)
+        sh[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < kReduceVals; ++k)
+                sh[threadIdx.x][k] = (k == 5) ? fmax(sh[threadIdx.x][k], sh[threadIdx.x + s][k])
+                                              : sh[threadIdx.x][k] + sh[threadIdx.x + s][k];
+        __syncthreads();
+    }
+    if (threadIdx.x < kReduceVals)
+        out[threadIdx.x] = sh[0][threadIdx.x];
+}
+
+// ---- host-side launch descriptors ---------------------------------------------
+enum Kind { K_STEP = 0, K_INIT = 1, K_MOMENTS = 2 };
+
+struct Launch {
+    int kind;
+    int storage;
+    int pattern;  // K_STEP: Pattern; K_MOMENTS: Form; K_INIT: 1 = AA slots
+    bool comp, force, uout;
+    const void *src;
+    void *dst;
+    StepParams sp;
+    const double *p0, *u0;
+    MomParams mp;
+    dim3 grid, block;
+    cudaStream_t stream;
+};
+
+template <class F>
+inline cudaError_t with_bool(bool b, F &&f)
+{
+    return b ? f(std::true_type{}) : f(std::false_type{});
+}
+
+template <class L, int S>
+cudaError_t launch_storage(const Launch &l)
+{
+    using T = typename Sto<S>::T;
+    const T *src = (const T *)l.src;
+    T *dst = (T *)l.dst;
+    if (l.kind == K_STEP) {
+        if (l.pattern == PAT_PULL) {
+            if (l.uout) {
+                // adjoint recompute: incompressible model only
+                return with_bool(l.force, [&](auto Fo) {
+                    k_step<L, S, PAT_PULL, false, decltype(Fo)::value, true>
+                        <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                    return cudaGetLastError();
+                });
+            }
+            return with_bool(l.comp, [&](auto C) {
+                return with_bool(l.force, [&](auto Fo) {
+                    k_step<L, S, PAT_PULL, decltype(C)::value, decltype(Fo)::value, false>
+                        <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                    return cudaGetLastError();
+                });
+            });
+        }
+        if (l.pattern == PAT_GATHER) {
+            return with_bool(l.comp, [&](auto C) {
+                return with_bool(l.force, [&](auto Fo) {
+                    k_step<L, S, PAT_GATHER, decltype(C)::value, decltype(Fo)::value, false>
+                        <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                    return cudaGetLastError();
+                });
+            });
+        }
+        return with_bool(l.comp, [&](auto C) {
+            return with_bool(l.force, [&](auto Fo) {
+                k_step<L, S, PAT_LOCAL, decltype(C)::value, decltype(Fo)::value, false>
+                    <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                return cudaGetLastError();
+            });
+        });
+    }
+    if (l.kind == K_INIT) {
+        return with_bool(l.pattern == 1, [&](auto AA) {
+            return with_bool(l.comp, [&](auto C) {
+                return with_bool(l.force, [&](auto Fo) {
+                    k_init<L, S, decltype(AA)::value, decltype(C)::value, decltype(Fo)::value>
+                        <<<l.grid, l.block, 0, l.stream>>>(dst, l.sp, l.p0, l.u0);
+                    return cudaGetLastError();
+                });
+            });
+        });
+    }
+    if (l.kind == K_MOMENTS) {
+        return with_bool(l.comp, [&](auto C) {
+            return with_bool(l.force, [&](auto Fo) {
+                constexpr bool c = decltype(C)::value, fo = decltype(Fo)::value;
+                switch (l.pattern) {
+                case FORM_LOCAL:
+                    k_moments<L, S, FORM_LOCAL, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, l.sp, l.mp);
+                    break;
+                case FORM_SWAPPED:
+                    k_moments<L, S, FORM_SWAPPED, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, l.sp, l.mp);
+                    break;
+                default:
+                    k_moments<L, S, FORM_STREAMED, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, l.sp, l.mp);
+                    break;
+                }
+                return cudaGetLastError();
+            });
+        });
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class L>
+cudaError_t launch_lattice(const Launch &l)
+{
+    switch (l.storage) {
+    case ST_F64:
+        return launch_storage<L, ST_F64>(l);
+    case ST_F32:
+        return launch_storage<L, ST_F32>(l);
+    case ST_F16S:
+        return launch_storage<L, ST_F16S>(l);
+    case ST_BF16S:
+        return launch_storage<L, ST_BF16S>(l);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Per-lattice entry points (one translation unit each).
+cudaError_t launch_d2q9(const Launch &l);
+cudaError_t launch_d3q19(const Launch &l);
+cudaError_t launch_d3q27(const Launch &l);
+cudaError_t launch_finish(const double *partials, int nblocks, double *out, cudaStream_t s);
+
+}  // namespace lbm

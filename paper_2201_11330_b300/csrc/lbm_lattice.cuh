@@ -1,0 +1,146 @@
+// lbm_lattice.cuh -- compile-time velocity sets and storage codecs.
+//
+// Velocity sets of Sec. 2.1 (arxiv 2201.11330).  D2Q9 follows the table the
+// paper prints: direction a = 3*(e_x+1) + (e_y+1), e_x slowest.  D3Q19 and
+// D3Q27 use the same lexicographic rule over (e_x, e_y, e_z) (the paper's
+// figure with their numbering is not recoverable); D3Q19 drops the eight
+// corners.  With this numbering the opposite of a is Q-1-a, the property
+// Sec. 2.1 designs its numbering for; a static_assert checks it.
+// Weights are Qian et al. (1992) by speed class |e|^2.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+#include <utility>
+
+namespace lbm {
+
+struct D2Q9 {
+    static constexpr int Q = 9, D = 2, ID = 0;
+    __host__ __device__ static constexpr int e(int a, int k)
+    {
+        return k == 0 ? a / 3 - 1 : (k == 1 ? a % 3 - 1 : 0);
+    }
+    __host__ __device__ static constexpr double w(int a)
+    {
+        return (e(a, 0) * e(a, 0) + e(a, 1) * e(a, 1)) == 0   ? 4.0 / 9.0
+               : (e(a, 0) * e(a, 0) + e(a, 1) * e(a, 1)) == 1 ? 1.0 / 9.0
+                                                              : 1.0 / 36.0;
+    }
+};
+
+struct D3Q27 {
+    static constexpr int Q = 27, D = 3, ID = 2;
+    __host__ __device__ static constexpr int e(int a, int k)
+    {
+        return k == 0 ? a / 9 - 1 : (k == 1 ? (a / 3) % 3 - 1 : a % 3 - 1);
+    }
+    __host__ __device__ static constexpr int s2(int a)
+    {
+        return e(a, 0) * e(a, 0) + e(a, 1) * e(a, 1) + e(a, 2) * e(a, 2);
+    }
+    __host__ __device__ static constexpr double w(int a)
+    {
+        return s2(a) == 0 ? 8.0 / 27.0 : s2(a) == 1 ? 2.0 / 27.0 : s2(a) == 2 ? 1.0 / 54.0 : 1.0 / 216.0;
+    }
+};
+
+struct D3Q19 {
+    static constexpr int Q = 19, D = 3, ID = 1;
+    // index of the a-th non-corner vector within the 3x3x3 lexicographic cube
+    __host__ __device__ static constexpr int cube(int a)
+    {
+        int k = 0;
+        for (int c = 0; c < 27; ++c) {
+            if (D3Q27::s2(c) == 3)
+                continue;
+            if (k == a)
+                return c;
+            ++k;
+        }
+        return -1;
+    }
+    __host__ __device__ static constexpr int e(int a, int k) { return D3Q27::e(cube(a), k); }
+    __host__ __device__ static constexpr double w(int a)
+    {
+        return D3Q27::s2(cube(a)) == 0 ? 1.0 / 3.0 : D3Q27::s2(cube(a)) == 1 ? 1.0 / 18.0 : 1.0 / 36.0;
+    }
+};
+
+template <class L>
+__host__ __device__ constexpr int opp(int a)
+{
+    return L::Q - 1 - a;
+}
+
+template <class L>
+constexpr bool check_set()
+{
+    double sw = 0.0;
+    for (int a = 0; a < L::Q; ++a) {
+        for (int k = 0; k < 3; ++k)
+            if (L::e(opp<L>(a), k) != -L::e(a, k))
+                return false;
+        sw += L::w(a);
+    }
+    return sw > 1.0 - 1e-12 && sw < 1.0 + 1e-12;
+}
+static_assert(check_set<D2Q9>(), "D2Q9 numbering");
+static_assert(check_set<D3Q19>(), "D3Q19 numbering");
+static_assert(check_set<D3Q27>(), "D3Q27 numbering");
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I in [B, E).
+template <int B, int E>
+struct SFor {
+    template <class F>
+    __host__ __device__ __forceinline__ static void run(F &&f)
+    {
+        if constexpr (B < E) {
+            f(std::integral_constant<int, B>{});
+            SFor<B + 1, E>::run(f);
+        }
+    }
+};
+
+// ---- storage codecs -------------------------------------------------------
+// Values are stored as (f_a - sigma*t_a) in T and decoded to the arithmetic
+// type R.  Encoding rounds to nearest even; decoding is exact.
+enum StorageId { ST_F64 = 0, ST_F32 = 1, ST_F16S = 2, ST_BF16S = 3 };
+
+template <int S>
+struct Sto;
+
+template <>
+struct Sto<ST_F64> {
+    using T = double;
+    using R = double;
+    __device__ __forceinline__ static R dec(T v) { return v; }
+    __device__ __forceinline__ static T enc(R v) { return v; }
+};
+template <>
+struct Sto<ST_F32> {
+    using T = float;
+    using R = float;
+    __device__ __forceinline__ static R dec(T v) { return v; }
+    __device__ __forceinline__ static T enc(R v) { return v; }
+};
+template <>
+struct Sto<ST_F16S> {
+    using T = unsigned short;
+    using R = float;
+    __device__ __forceinline__ static R dec(T v) { return __half2float(__ushort_as_half(v)); }
+    __device__ __forceinline__ static T enc(R v) { return __half_as_ushort(__float2half_rn(v)); }
+};
+template <>
+struct Sto<ST_BF16S> {
+    using T = unsigned short;
+    using R = float;
+    __device__ __forceinline__ static R dec(T v) { return __bfloat162float(__ushort_as_bfloat16(v)); }
+    __device__ __forceinline__ static T enc(R v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+};
+
+}  // namespace lbm

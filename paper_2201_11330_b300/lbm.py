@@ -1,0 +1,392 @@
+"""Python binding of the C ABI in include/lbm.h (ctypes, argument marshalling only).
+
+Every step of the hot path runs in liblbm.so's CUDA kernels; this module only
+converts arguments.  PyTorch provides device memory (the workspace and the
+field tensors) and the current CUDA stream.  There is no CPU fallback: if the
+library is missing or no GPU is present, the calls raise.
+
+Two layers:
+  * module functions with the C names (lbm_create, lbm_init, lbm_step, ...),
+    taking plain ints / pointers, and
+  * ``Lattice``, a small owner object that allocates the workspace with torch
+    and calls those functions.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbm.so")
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_STATE, LBM_ERR_NOMEM = 0, -1, -2, -3, -4, -5
+LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 = 0, 1, 2
+LBM_BC_PERIODIC, LBM_BC_CAVITY, LBM_BC_CHANNEL = 0, 1, 2
+LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = 0, 1, 2, 3
+
+LATTICES = {"d2q9": LBM_D2Q9, "d3q19": LBM_D3Q19, "d3q27": LBM_D3Q27}
+BCS = {"periodic": LBM_BC_PERIODIC, "cavity": LBM_BC_CAVITY, "channel": LBM_BC_CHANNEL}
+STORAGES = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "bf16s": LBM_BF16S}
+QD = {LBM_D2Q9: (9, 2), LBM_D3Q19: (19, 3), LBM_D3Q27: (27, 3)}
+
+# Every extern "C" symbol include/lbm.h declares.
+EXPORTS = [
+    "lbm_default_opts", "lbm_tau_from_paper", "lbm_workspace_bytes", "lbm_create",
+    "lbm_set_stream", "lbm_init", "lbm_set_force", "lbm_set_lid", "lbm_step",
+    "lbm_step_count", "lbm_macroscopic", "lbm_reduce", "lbm_state_bytes", "lbm_get_state",
+    "lbm_set_state", "lbm_adjoint_workspace_bytes", "lbm_adjoint_forward",
+    "lbm_adjoint_backward", "lbm_adjoint", "lbm_error_string", "lbm_destroy",
+]
+
+
+class lbm_opts(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int), ("aa", ctypes.c_int), ("compressible", ctypes.c_int),
+                ("f32_unshifted", ctypes.c_int), ("rho0", ctypes.c_double),
+                ("lid_u", ctypes.c_double * 3), ("has_force", ctypes.c_int)]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {lbm_error_string(status)} (status {status})")
+        self.status = status
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64 = ctypes.c_int64
+_sz = ctypes.c_size_t
+
+
+def load():
+    """Load liblbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"{LIB_PATH} is missing: build it with `python -m paper_2201_11330_b300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    ip = ctypes.c_int
+    op = ctypes.POINTER(lbm_opts)
+    sig = {
+        "lbm_default_opts": (None, [op]),
+        "lbm_tau_from_paper": (ctypes.c_double, [ctypes.c_double]),
+        "lbm_workspace_bytes": (_sz, [ip, ip, ip, ip, op]),
+        "lbm_create": (ip, [ip, ip, ip, ip, ctypes.c_double, ip, op, _vp, _sz, _vp,
+                            ctypes.POINTER(_vp)]),
+        "lbm_set_stream": (ip, [_vp, _vp]),
+        "lbm_init": (ip, [_vp, _vp, _vp]),
+        "lbm_set_force": (ip, [_vp, _vp]),
+        "lbm_set_lid": (ip, [_vp, _dp]),
+        "lbm_step": (ip, [_vp, _i64]),
+        "lbm_step_count": (_i64, [_vp]),
+        "lbm_macroscopic": (ip, [_vp, _vp, _vp, ip]),
+        "lbm_reduce": (ip, [_vp, _dp]),
+        "lbm_state_bytes": (_sz, [_vp]),
+        "lbm_get_state": (ip, [_vp, _vp, ctypes.POINTER(_i64)]),
+        "lbm_set_state": (ip, [_vp, _vp, _i64]),
+        "lbm_adjoint_workspace_bytes": (_sz, [_vp, _i64, _i64]),
+        "lbm_adjoint_forward": (ip, [_vp, _i64, _i64, _vp, _sz, _dp]),
+        "lbm_adjoint_backward": (ip, [_vp, _vp, _sz, _vp, _dp]),
+        "lbm_adjoint": (ip, [_vp, _i64, _i64, _vp, _sz, _dp, _vp, _dp]),
+        "lbm_error_string": (ctypes.c_char_p, [ip]),
+        "lbm_destroy": (None, [_vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+# ---- C names, marshalling only -------------------------------------------------
+
+def lbm_default_opts() -> lbm_opts:
+    o = lbm_opts()
+    load().lbm_default_opts(ctypes.byref(o))
+    return o
+
+
+def lbm_tau_from_paper(tau_paper: float) -> float:
+    return load().lbm_tau_from_paper(tau_paper)
+
+
+def lbm_workspace_bytes(lattice: int, nx: int, ny: int, nz: int, opts: lbm_opts) -> int:
+    return load().lbm_workspace_bytes(lattice, nx, ny, nz, ctypes.byref(opts))
+
+
+def lbm_create(lattice, nx, ny, nz, tau, bc, opts, workspace_ptr, nbytes, stream_ptr):
+    ctx = _vp()
+    rc = load().lbm_create(lattice, nx, ny, nz, tau, bc, ctypes.byref(opts), workspace_ptr,
+                           nbytes, stream_ptr, ctypes.byref(ctx))
+    _check(rc, "lbm_create")
+    return ctx
+
+
+def lbm_set_stream(ctx, stream_ptr):
+    _check(load().lbm_set_stream(ctx, stream_ptr), "lbm_set_stream")
+
+
+def lbm_init(ctx, p_ptr, u_ptr):
+    _check(load().lbm_init(ctx, p_ptr, u_ptr), "lbm_init")
+
+
+def lbm_set_force(ctx, force_ptr):
+    _check(load().lbm_set_force(ctx, force_ptr), "lbm_set_force")
+
+
+def lbm_set_lid(ctx, lid3):
+    arr = (ctypes.c_double * 3)(*[float(v) for v in lid3])
+    _check(load().lbm_set_lid(ctx, arr), "lbm_set_lid")
+
+
+def lbm_step(ctx, n: int):
+    _check(load().lbm_step(ctx, int(n)), "lbm_step")
+
+
+def lbm_step_count(ctx) -> int:
+    return load().lbm_step_count(ctx)
+
+
+def lbm_macroscopic(ctx, p_ptr, u_ptr, out_dtype: int):
+    _check(load().lbm_macroscopic(ctx, p_ptr, u_ptr, out_dtype), "lbm_macroscopic")
+
+
+def lbm_reduce(ctx):
+    out = (ctypes.c_double * 6)()
+    _check(load().lbm_reduce(ctx, out), "lbm_reduce")
+    return list(out)
+
+
+def lbm_state_bytes(ctx) -> int:
+    return load().lbm_state_bytes(ctx)
+
+
+def lbm_get_state(ctx, dst_ptr) -> int:
+    step = _i64()
+    _check(load().lbm_get_state(ctx, dst_ptr, ctypes.byref(step)), "lbm_get_state")
+    return step.value
+
+
+def lbm_set_state(ctx, src_ptr, step: int):
+    _check(load().lbm_set_state(ctx, src_ptr, int(step)), "lbm_set_state")
+
+
+def lbm_adjoint_workspace_bytes(ctx, T: int, K: int) -> int:
+    return load().lbm_adjoint_workspace_bytes(ctx, int(T), int(K))
+
+
+def lbm_adjoint_forward(ctx, T, K, ws_ptr, nbytes) -> float:
+    J = ctypes.c_double()
+    _check(load().lbm_adjoint_forward(ctx, int(T), int(K), ws_ptr, nbytes, ctypes.byref(J)),
+           "lbm_adjoint_forward")
+    return J.value
+
+
+def lbm_adjoint_backward(ctx, ws_ptr, nbytes, dJdF_ptr):
+    gU = (ctypes.c_double * 3)()
+    _check(load().lbm_adjoint_backward(ctx, ws_ptr, nbytes, dJdF_ptr, gU), "lbm_adjoint_backward")
+    return list(gU)
+
+
+def lbm_adjoint(ctx, T, K, ws_ptr, nbytes, dJdF_ptr):
+    J = ctypes.c_double()
+    gU = (ctypes.c_double * 3)()
+    _check(load().lbm_adjoint(ctx, int(T), int(K), ws_ptr, nbytes, ctypes.byref(J), dJdF_ptr, gU),
+           "lbm_adjoint")
+    return J.value, list(gU)
+
+
+def lbm_error_string(status: int) -> str:
+    return load().lbm_error_string(int(status)).decode()
+
+
+def lbm_destroy(ctx):
+    load().lbm_destroy(ctx)
+
+
+def _check(rc: int, where: str):
+    if rc != LBM_OK:
+        raise LBMError(rc, where)
+
+
+# ---- owner object ----------------------------------------------------------------
+
+def _key(table, v):
+    return table[v] if isinstance(v, str) else int(v)
+
+
+class Lattice:
+    """A simulation context whose workspace is a torch tensor on `device`.
+
+    Fields exchanged with it are torch tensors on the same device: pressure
+    (N,), velocity (d, N) in FP64 (or FP32 for outputs on request), force
+    (d, N) in FP32.  Calls launch on torch's current stream.
+    """
+
+    def __init__(self, lattice, nx, ny, nz, tau, bc, *, storage="f32", aa=False,
+                 compressible=False, f32_unshifted=False, rho0=1.0, lid=(0.0, 0.0, 0.0),
+                 has_force=False, device="cuda"):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the LBM library needs a CUDA device")
+        self.torch = torch
+        self.lattice = _key(LATTICES, lattice)
+        self.Q, self.d = QD[self.lattice]
+        self.shape = (int(nx), int(ny), int(nz))
+        self.N = int(nx) * int(ny) * int(nz)
+        self.tau = float(tau)
+        self.bc = _key(BCS, bc)
+        self.device = torch.device(device)
+        o = lbm_default_opts()
+        o.storage = _key(STORAGES, storage)
+        o.aa = int(bool(aa))
+        o.compressible = int(bool(compressible))
+        o.f32_unshifted = int(bool(f32_unshifted))
+        o.rho0 = float(rho0)
+        lid = list(lid) + [0.0] * (3 - len(lid))
+        for k in range(3):
+            o.lid_u[k] = float(lid[k])
+        o.has_force = int(bool(has_force))
+        self.opts = o
+        nbytes = lbm_workspace_bytes(self.lattice, nx, ny, nz, o)
+        if nbytes == 0:
+            raise LBMError(LBM_ERR_ARG, "lbm_workspace_bytes")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.ctx = lbm_create(self.lattice, nx, ny, nz, self.tau, self.bc, o,
+                              self.workspace.data_ptr(), nbytes, self._stream())
+        self._force = None
+        self._adj_ws = None
+
+    def _stream(self):
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    def _sync_stream(self):
+        lbm_set_stream(self.ctx, self._stream())
+
+    def _dev(self, t, dtype, numel):
+        torch = self.torch
+        t = torch.as_tensor(t, dtype=dtype, device=self.device).contiguous()
+        if t.numel() != numel:
+            raise ValueError(f"expected {numel} values, got {t.numel()}")
+        return t
+
+    def init(self, p=None, u=None):
+        """f = feq(p, u) (Sec. 2.2); p (N,) and u (d, N) FP64, None = 1/3 and 0."""
+        torch = self.torch
+        self._sync_stream()
+        pt = None if p is None else self._dev(p, torch.float64, self.N)
+        ut = None if u is None else self._dev(u, torch.float64, self.d * self.N)
+        lbm_init(self.ctx, None if pt is None else pt.data_ptr(),
+                 None if ut is None else ut.data_ptr())
+        # keep the inputs alive until the init kernel has consumed them
+        self._init_inputs = (pt, ut)
+        return self
+
+    def set_force(self, F):
+        """Body force (d, N) FP32 on the device (None removes it)."""
+        torch = self.torch
+        if F is None:
+            lbm_set_force(self.ctx, None)
+            self._force = None
+            return self
+        Ft = self._dev(F, torch.float32, self.d * self.N)
+        lbm_set_force(self.ctx, Ft.data_ptr())
+        self._force = Ft
+        return self
+
+    def set_lid(self, lid):
+        lbm_set_lid(self.ctx, list(lid) + [0.0] * (3 - len(lid)))
+        return self
+
+    def step(self, n=1):
+        self._sync_stream()
+        lbm_step(self.ctx, n)
+        return self
+
+    @property
+    def step_count(self):
+        return lbm_step_count(self.ctx)
+
+    def macroscopic(self, dtype=None):
+        """(p (N,), u (d, N)) of the current step."""
+        torch = self.torch
+        dtype = dtype or torch.float64
+        self._sync_stream()
+        p = torch.empty(self.N, dtype=dtype, device=self.device)
+        u = torch.empty((self.d, self.N), dtype=dtype, device=self.device)
+        lbm_macroscopic(self.ctx, p.data_ptr(), u.data_ptr(), 1 if dtype == torch.float32 else 0)
+        return p, u
+
+    def macroscopic_into(self, p, u):
+        """Write p and u of the current step into preallocated tensors."""
+        torch = self.torch
+        self._sync_stream()
+        dt = (p if p is not None else u).dtype
+        lbm_macroscopic(self.ctx, None if p is None else p.data_ptr(),
+                        None if u is None else u.data_ptr(), 1 if dt == torch.float32 else 0)
+
+    def reduce(self):
+        """dict(mass, momentum (3,), kinetic_energy, max_speed), FP64."""
+        self._sync_stream()
+        r = lbm_reduce(self.ctx)
+        return {"mass": r[0], "momentum": r[1:4], "kinetic_energy": r[4], "max_speed": r[5]}
+
+    def state_bytes(self):
+        return lbm_state_bytes(self.ctx)
+
+    def get_state(self):
+        torch = self.torch
+        self._sync_stream()
+        buf = torch.empty(self.state_bytes(), dtype=torch.uint8, device=self.device)
+        step = lbm_get_state(self.ctx, buf.data_ptr())
+        return buf, step
+
+    def set_state(self, buf, step):
+        self._sync_stream()
+        lbm_set_state(self.ctx, buf.data_ptr(), step)
+        return self
+
+    def adjoint_workspace(self, T, K):
+        torch = self.torch
+        nbytes = lbm_adjoint_workspace_bytes(self.ctx, T, K)
+        if nbytes == 0:
+            raise LBMError(LBM_ERR_ARG, "lbm_adjoint_workspace_bytes")
+        if self._adj_ws is None or self._adj_ws.numel() < nbytes:
+            self._adj_ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        return self._adj_ws
+
+    def adjoint_forward(self, T, K):
+        ws = self.adjoint_workspace(T, K)
+        self._sync_stream()
+        return lbm_adjoint_forward(self.ctx, T, K, ws.data_ptr(), ws.numel())
+
+    def adjoint_backward(self):
+        torch = self.torch
+        self._sync_stream()
+        g = torch.empty((self.d, self.N), dtype=torch.float64, device=self.device)
+        gU = lbm_adjoint_backward(self.ctx, self._adj_ws.data_ptr(), self._adj_ws.numel(),
+                                  g.data_ptr())
+        return g, torch.tensor(gU, dtype=torch.float64)
+
+    def adjoint(self, T, K):
+        """(J, dJ/dF (d, N) FP64 on device, dJ/dU (3,) FP64 on host)."""
+        torch = self.torch
+        ws = self.adjoint_workspace(T, K)
+        self._sync_stream()
+        g = torch.empty((self.d, self.N), dtype=torch.float64, device=self.device)
+        J, gU = lbm_adjoint(self.ctx, T, K, ws.data_ptr(), ws.numel(), g.data_ptr())
+        return J, g, torch.tensor(gU, dtype=torch.float64)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

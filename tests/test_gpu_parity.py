@@ -1,0 +1,293 @@
+"""GPU (CUDA path through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: FP64 fields 1e-12, FP32 velocity 1e-5, shifted half storage 2e-3,
+all as max_x |a - b| / scale with scale = U_ref for velocity and
+rho0 U_ref^2 for pressure.  Both sides get identical seeded inputs; the
+force field is FP32 on both (the oracle reads it widened to FP64).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2201_11330_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_11330_b300 import build
+    build.build()
+
+
+def gpu_run(lattice, shape, tau, bc, steps, *, storage="f64", aa=False, lid=None, F=None,
+            p0=None, u0=None, compressible=False, rho0=1.0, f32_unshifted=False):
+    from paper_2201_11330_b300.lbm import Lattice
+    nx, ny, nz = shape
+    lat = Lattice(lattice, nx, ny, nz, tau, bc, storage=storage, aa=aa,
+                  compressible=compressible, rho0=rho0, lid=lid or (0, 0, 0),
+                  has_force=F is not None, f32_unshifted=f32_unshifted)
+    if F is not None:
+        lat.set_force(torch.from_numpy(np.ascontiguousarray(F, dtype=np.float32)).cuda())
+    lat.init(None if p0 is None else torch.from_numpy(p0).cuda(),
+             None if u0 is None else torch.from_numpy(np.ascontiguousarray(u0)).cuda())
+    lat.step(steps)
+    p, u = lat.macroscopic()
+    out = p.cpu().numpy(), u.cpu().numpy(), lat
+    torch.cuda.synchronize()
+    return out
+
+
+def oracle_run(lattice, shape, tau, bc, steps, *, lid=None, F=None, p0=None, u0=None,
+               compressible=False, rho0=1.0):
+    nx, ny, nz = shape
+    F64 = None if F is None else np.asarray(F, dtype=np.float32).astype(np.float64)
+    return oracle.run(lattice, nx, ny, nz, tau, bc, steps, lid=lid, F=F64, p0=p0,
+                      u0=None if u0 is None else np.ascontiguousarray(u0).ravel(),
+                      compressible=compressible, rho0=rho0)
+
+
+def errors(gpu, ref, uref, rho0=1.0):
+    pg, ug = gpu[0], gpu[1]
+    pr, ur = ref
+    eu = np.abs(ug - ur).max() / uref
+    ep = np.abs(pg - pr).max() / (rho0 * uref * uref)
+    return eu, ep
+
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16s": 2e-3}
+
+
+# ---------------------------------------------------------------------------
+# D2Q9 lid-driven cavity 64 x 64, FP64, Re = 100, 1000 steps
+
+
+@pytest.fixture(scope="module")
+def cavity2d_ref():
+    c = W.cavity_params(64, 100.0, 0.1)
+    return c, oracle_run("d2q9", (64, 64, 1), c["tau"], "cavity", 1000, lid=c["lid"])
+
+
+@pytest.mark.parametrize("aa", [False, True])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_cavity2d_64(cavity2d_ref, aa, storage):
+    c, ref = cavity2d_ref
+    got = gpu_run("d2q9", (64, 64, 1), c["tau"], "cavity", 1000, storage=storage, aa=aa,
+                  lid=c["lid"])
+    eu, ep = errors(got, ref, 0.1)
+    assert eu < TOL[storage] and ep < (TOL[storage] if storage == "f64" else 1e-4), (eu, ep)
+
+
+# ---------------------------------------------------------------------------
+# Ragged multi-tile 3D boxes with random initial states, every BC and lattice
+
+
+CASES3D = [
+    ("d3q19", (37, 29, 23), "cavity"),
+    ("d3q19", (300, 7, 5), "channel"),
+    ("d3q19", (33, 17, 19), "periodic"),
+    ("d3q27", (35, 21, 13), "cavity"),
+    ("d3q27", (19, 11, 9), "periodic"),
+    ("d3q27", (41, 9, 6), "channel"),
+    ("d2q9", (301, 67, 1), "cavity"),
+    ("d2q9", (45, 33, 1), "periodic"),
+    ("d2q9", (29, 17, 1), "channel"),
+]
+
+
+@pytest.mark.parametrize("lattice,shape,bc", CASES3D)
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("aa", [False, True])
+def test_random_state_parity(lattice, shape, bc, storage, aa):
+    Q, d = oracle.dims(lattice)
+    nx, ny, nz = shape
+    p0, u0 = W.random_smooth_state(nx, ny, nz, d, amp_u=0.04, amp_p=2e-3, seed=21)
+    lid = (0.08, 0.0, 0.02) if bc != "periodic" else None
+    F = W.fourier_force(nx, ny, nz, amplitude=2e-5, seed=5, dims=d)
+    steps = 61  # odd: the AA state ends in its streamed form
+    ref = oracle_run(lattice, shape, 0.62, bc, steps, lid=lid, F=F, p0=p0, u0=u0)
+    got = gpu_run(lattice, shape, 0.62, bc, steps, storage=storage, aa=aa, lid=lid, F=F,
+                  p0=p0, u0=u0)
+    eu, ep = errors(got, ref, 0.05)
+    assert eu < TOL[storage] and ep < 10 * TOL[storage], (eu, ep)
+
+
+@pytest.mark.parametrize("lattice,shape,bc", [("d3q19", (21, 18, 14), "cavity"),
+                                              ("d2q9", (40, 31, 1), "periodic"),
+                                              ("d3q27", (15, 13, 12), "channel")])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_compressible_parity(lattice, shape, bc, storage):
+    Q, d = oracle.dims(lattice)
+    nx, ny, nz = shape
+    p0, u0 = W.random_smooth_state(nx, ny, nz, d, amp_u=0.04, amp_p=5e-3, seed=8)
+    lid = (0.05, 0.0, 0.0) if bc != "periodic" else None
+    F = W.fourier_force(nx, ny, nz, amplitude=1e-5, seed=6, dims=d)
+    for steps in (40, 41):
+        ref = oracle_run(lattice, shape, 0.7, bc, steps, lid=lid, F=F, p0=p0, u0=u0,
+                         compressible=True)
+        for aa in (False, True):
+            got = gpu_run(lattice, shape, 0.7, bc, steps, storage=storage, aa=aa, lid=lid, F=F,
+                          p0=p0, u0=u0, compressible=True)
+            eu, ep = errors(got, ref, 0.05)
+            assert eu < TOL[storage] and ep < 10 * TOL[storage], (steps, aa, eu, ep)
+
+
+def test_rho0_and_unshifted_f32():
+    shape = (23, 19, 11)
+    p0, u0 = W.random_smooth_state(*shape, 3, amp_u=0.03, seed=4)
+    ref = oracle_run("d3q19", shape, 0.75, "cavity", 30, lid=(0.05, 0, 0), p0=p0, u0=u0, rho0=1.3)
+    for unshifted in (False, True):
+        got = gpu_run("d3q19", shape, 0.75, "cavity", 30, storage="f32", lid=(0.05, 0, 0),
+                      p0=p0, u0=u0, rho0=1.3, f32_unshifted=unshifted)
+        eu, _ = errors(got, ref, 0.05, rho0=1.3)
+        assert eu < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Edge cases
+
+
+@pytest.mark.parametrize("lattice,shape,bc", [("d3q19", (1, 1, 1), "periodic"),
+                                              ("d3q27", (1, 1, 1), "cavity"),
+                                              ("d2q9", (1, 1, 1), "channel"),
+                                              ("d3q19", (3, 3, 3), "cavity"),
+                                              ("d3q27", (2, 3, 2), "periodic"),
+                                              ("d2q9", (3, 3, 1), "cavity"),
+                                              ("d3q19", (1, 16, 1), "channel"),
+                                              ("d3q19", (2, 1, 5), "periodic")])
+@pytest.mark.parametrize("aa", [False, True])
+def test_tiny_grids(lattice, shape, bc, aa):
+    Q, d = oracle.dims(lattice)
+    p0, u0 = W.random_smooth_state(*shape, d, amp_u=0.03, seed=2)
+    lid = (0.05, 0, 0.01) if bc != "periodic" else None
+    F = np.full((d, int(np.prod(shape))), 1e-5, dtype=np.float32)
+    for steps in (0, 1, 2, 7):
+        ref = oracle_run(lattice, shape, 0.7, bc, steps, lid=lid, F=F, p0=p0, u0=u0)
+        got = gpu_run(lattice, shape, 0.7, bc, steps, storage="f64", aa=aa, lid=lid, F=F,
+                      p0=p0, u0=u0)
+        eu, ep = errors(got, ref, 0.05)
+        assert eu < 1e-12 and ep < 1e-11, (steps, eu, ep)
+
+
+def test_poiseuille_on_gpu():
+    """Channel with a body force at (tau - 1/2)^2 = 3/16: exact parabola."""
+    ny, G = 14, 1e-6
+    tau = 0.5 + math.sqrt(3 / 16)
+    nu = W.viscosity(tau)
+    F = np.zeros((3, ny), dtype=np.float32)
+    F[0] = G
+    _, u, _ = gpu_run("d3q19", (1, ny, 1), tau, "channel", int(25 * ny * ny / nu), storage="f64",
+                      F=F)
+    y = np.arange(ny)
+    parabola = np.float64(np.float32(G)) / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    assert np.abs(u[0] - parabola).max() < 1e-9 * parabola.max()
+
+
+# ---------------------------------------------------------------------------
+# AA against the pull scheme: same arithmetic, bitwise equal
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s", "bf16s"])
+@pytest.mark.parametrize("bc", ["cavity", "periodic", "channel"])
+def test_aa_equals_pull_bitwise(storage, bc):
+    shape = (45, 26, 19)
+    p0, u0 = W.random_smooth_state(*shape, 3, amp_u=0.04, seed=12)
+    lid = (0.07, 0, 0) if bc != "periodic" else None
+    for steps in (10, 11):
+        a = gpu_run("d3q19", shape, 0.6, bc, steps, storage=storage, aa=False, lid=lid, p0=p0, u0=u0)
+        b = gpu_run("d3q19", shape, 0.6, bc, steps, storage=storage, aa=True, lid=lid, p0=p0, u0=u0)
+        if lid is not None and storage in ("f16s", "bf16s"):
+            # the AA pattern rounds f* + lid term once where the pull scheme
+            # rounds f* alone: equal to within one storage rounding there
+            assert np.abs(a[1] - b[1]).max() < 1e-2 * 0.07
+        else:
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+# ---------------------------------------------------------------------------
+# Reductions, checkpoint / resume, failure detection
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("aa", [False, True])
+def test_reduce_matches_fields(storage, aa):
+    shape = (50, 40, 30)
+    p0, u0 = W.random_smooth_state(*shape, 3, amp_u=0.05, seed=3)
+    for steps in (12, 13):
+        p, u, lat = gpu_run("d3q19", shape, 0.7, "cavity", steps, storage=storage, aa=aa,
+                            lid=(0.1, 0, 0), p0=p0, u0=u0)
+        r = lat.reduce()
+        N = p.size
+        tol = 1e-12 if storage == "f64" else 2e-6
+        assert abs(r["mass"] - 3 * p.sum()) <= tol * N
+        assert np.allclose(r["momentum"], u.sum(axis=1), atol=tol * N * 0.05, rtol=0)
+        assert abs(r["kinetic_energy"] - 0.5 * (u * u).sum()) <= tol * 0.5 * (u * u).sum() + 1e-300
+        assert abs(r["max_speed"] - np.sqrt((u * u).sum(axis=0)).max()) <= tol
+        # closed cavity: mass is conserved
+        assert abs(r["mass"] - 3 * p0.sum()) <= (1e-12 if storage == "f64" else 1e-6) * N
+
+
+@pytest.mark.parametrize("aa", [False, True])
+def test_checkpoint_resume_bitwise(aa):
+    shape = (40, 33, 21)
+    p0, u0 = W.random_smooth_state(*shape, 3, amp_u=0.05, seed=30)
+    pa, ua, _ = gpu_run("d3q19", shape, 0.6, "cavity", 40, storage="f32", aa=aa,
+                        lid=(0.1, 0, 0), p0=p0, u0=u0)
+    _, _, lat = gpu_run("d3q19", shape, 0.6, "cavity", 15, storage="f32", aa=aa,
+                        lid=(0.1, 0, 0), p0=p0, u0=u0)
+    buf, step = lat.get_state()
+    assert step == 15
+    lat.step(7)  # wander off, then restore
+    lat.set_state(buf, step)
+    lat.step(25)
+    pb, ub = lat.macroscopic()
+    assert np.array_equal(pa, pb.cpu().numpy()) and np.array_equal(ua, ub.cpu().numpy())
+
+
+def test_nan_is_reported_as_unstable():
+    from paper_2201_11330_b300.lbm import LBMError, LBM_ERR_UNSTABLE
+    shape = (16, 16, 16)
+    p0, u0 = W.random_smooth_state(*shape, 3, seed=1)
+    u0 = u0.copy()
+    u0[0, 100] = np.nan
+    _, _, lat = gpu_run("d3q19", shape, 0.7, "cavity", 3, storage="f32", p0=p0, u0=u0)
+    with pytest.raises(LBMError) as ei:
+        lat.reduce()
+    assert ei.value.status == LBM_ERR_UNSTABLE
+
+
+# ---------------------------------------------------------------------------
+# Taylor-Green vortex 512 x 512, 5000 steps: oracle parity and analytic decay
+
+
+@pytest.fixture(scope="module")
+def tgv512_ref():
+    n = 512
+    p0, u0 = W.taylor_green_2d(n, n, 0.05)
+    ref = oracle_run("d2q9", (n, n, 1), 0.8, "periodic", 5000, p0=p0, u0=u0)
+    return p0, u0, ref
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_taylor_green_512(tgv512_ref, storage):
+    p0, u0, ref = tgv512_ref
+    n = 512
+    got = gpu_run("d2q9", (n, n, 1), 0.8, "periodic", 5000, storage=storage, aa=True, p0=p0, u0=u0)
+    eu, ep = errors(got, ref, 0.05)
+    assert eu < TOL[storage], eu
+    # analytic decay of the amplitude, exp(-nu (kx^2 + ky^2) t)
+    x, y, _ = W.grid(n, n, 1)
+    k = 2 * math.pi / n
+    mode = -np.cos(k * x) * np.sin(k * y)
+    amp = (got[1][0] * mode).sum() / (mode * mode).sum() / 0.05
+    assert abs(amp / math.exp(-W.taylor_green_rate(n, n, 0.8) * 5000) - 1) < 0.01
+    # exact conservation on the periodic box
+    lat = got[2]
+    r = lat.reduce()
+    assert abs(r["mass"] - 3 * p0.sum()) <= (1e-12 if storage == "f64" else 1e-6) * n * n
