@@ -161,7 +161,11 @@ Launch base_launch(const lbm_ctx *c, int kind)
 // ---- internal helpers shared with the adjoint driver ------------------------
 namespace lbm {
 
-int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, float *u_out)
+Launch ctx_base_launch(const lbm_ctx *c, int kind) { return base_launch(c, kind); }
+
+cudaError_t ctx_dispatch(const lbm_ctx *c, const Launch &l) { return dispatch(c->lattice, l); }
+
+int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u_out)
 {
     Launch l = base_launch(c, K_STEP);
     l.pattern = pattern;

@@ -30,10 +30,17 @@ struct lbm_ctx {
     int bx;  // threads per block along x
     bool initialized;
     lbm::StepParams sp;
+    // adjoint run recorded by lbm_adjoint_forward for lbm_adjoint_backward
+    int64_t adj_T, adj_K;
+    void *adj_ws;
+    size_t adj_bytes;
+    bool adj_ready;
 };
 
 namespace lbm {
-int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, float *u_out);
+lbm::Launch ctx_base_launch(const lbm_ctx *c, int kind);
+cudaError_t ctx_dispatch(const lbm_ctx *c, const lbm::Launch &l);
+int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u_out);
 int ctx_launch_moments(lbm_ctx *c, const void *src, int form, void *p_out, void *u_out,
                        int out_f32, double *partials);
 int ctx_current_form(const lbm_ctx *c);

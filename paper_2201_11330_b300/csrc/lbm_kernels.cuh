@@ -52,7 +52,7 @@ struct StepParams {
     Coef<float> cf;
     Coef<double> cd;
     const float *F;  // body force, d*N component-major (FORCE kernels)
-    float *u_out;    // velocity output, d*N component-major (UOUT kernels)
+    void *u_out;     // velocity output, d*N component-major, kernel arithmetic type (UOUT)
 };
 
 template <class R>
@@ -285,9 +285,19 @@ __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typenam
 
     R g[Q];
     if constexpr (PAT == PAT_LOCAL) {
+        // Slot a of x holds the population entering x along e_a; on the top
+        // row every e_y = -1 population has crossed the moving wall, and its
+        // lid term is added here, at read time, exactly as the pull scheme
+        // does, so that both schemes round identically.
+        const bool top = p.lid_on && (y == p.ny - 1);
         SFor<0, Q>::run([&](auto A_) {
             constexpr int a = decltype(A_)::value;
-            g[a] = Sto<S>::dec(ld(src + a * N + n));
+            R v = Sto<S>::dec(ld(src + a * N + n));
+            if constexpr (L::e(a, 1) == -1) {
+                if (top)
+                    v += c.lid[a];
+            }
+            g[a] = v;
         });
     } else {
         SFor<0, Q>::run([&](auto A_) {
@@ -321,7 +331,7 @@ __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typenam
     if constexpr (UOUT) {
         SFor<0, L::D>::run([&](auto K_) {
             constexpr int k = decltype(K_)::value;
-            p.u_out[k * N + n] = float(u[k]);
+            ((R *)p.u_out)[k * N + n] = u[k];
         });
     }
     SFor<0, Q>::run([&](auto A_) {
@@ -337,12 +347,9 @@ __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typenam
             bool wall;
             upstream<L, b>(X, Y, Z, off, wall);
             if (wall) {
-                R v = g[a];
-                if constexpr (L::e(b, 1) == -1) {
-                    if (lid_row)
-                        v += c.lid[b];
-                }
-                st(dst + b * N + n, Sto<S>::enc(v));
+                // bounced: stays at x as the population entering along e_b
+                // (its lid term, if any, is added when it is read)
+                st(dst + b * N + n, Sto<S>::enc(g[a]));
             } else {
                 st(dst + a * N + (n + off), Sto<S>::enc(g[a]));
             }
@@ -483,7 +490,6 @@ __global__ void __launch_bounds__(256) k_moments(const typename Sto<S>::T *src, 
             } else {
                 AxisNbr X, Y, Z;
                 make_axes<L, false>(p, x, y, z, X, Y, Z);
-                const bool lid_row = p.lid_on && (y == p.ny - 1);
                 SFor<0, Q>::run([&](auto A_) {
                     constexpr int a = decltype(A_)::value;
                     constexpr int b = opp<L>(a);
@@ -491,12 +497,7 @@ __global__ void __launch_bounds__(256) k_moments(const typename Sto<S>::T *src, 
                     bool wall;
                     upstream<L, b>(X, Y, Z, off, wall);
                     if (wall) {
-                        R v = Sto<S>::dec(src[b * N + n]);
-                        if constexpr (L::e(b, 1) == -1) {
-                            if (lid_row)
-                                v -= c.lid[b];
-                        }
-                        g[a] = v;
+                        g[a] = Sto<S>::dec(src[b * N + n]);
                     } else {
                         g[a] = Sto<S>::dec(src[a * N + (n + off)]);
                     }
@@ -602,8 +603,20 @@ static __global__ void __launch_bounds__(256) k_reduce_finish(const double *part
         out[threadIdx.x] = sh[0][threadIdx.x];
 }
 
-// ---- host-side launch descriptors ---------------------------------------------
-enum Kind { K_STEP = 0, K_INIT = 1, K_MOMENTS = 2 };
+// ---- adjoint parameters (kernels in lbm_adjoint.cuh) -------------------------
+struct AdjParams {
+    const void *lam_in;   // lambda^{k+1}, Q*N (R)
+    void *lam_out;        // lambda^k, Q*N (R)
+    const void *u_k;      // u^k, d*N (R)
+    void *gF;             // per-segment force gradient, d*N (R), accumulated
+    double *gU_part;      // per top-row block: 4 doubles, accumulated over steps
+    const void *state;    // seed: final post-collision state (pull-scheme layout)
+    double *dJdF;         // segment flush: FP64 total, d*N
+    int xseg;
+};
+
+// ---- host-side launch descriptors ----------------------------------------------
+enum Kind { K_STEP = 0, K_INIT = 1, K_MOMENTS = 2, K_ADJ = 3, K_SEED = 4, K_FLUSH = 5 };
 
 struct Launch {
     int kind;
@@ -615,105 +628,11 @@ struct Launch {
     StepParams sp;
     const double *p0, *u0;
     MomParams mp;
+    AdjParams ap;
+    size_t count;  // K_FLUSH
     dim3 grid, block;
     cudaStream_t stream;
 };
-
-template <class F>
-inline cudaError_t with_bool(bool b, F &&f)
-{
-    return b ? f(std::true_type{}) : f(std::false_type{});
-}
-
-template <class L, int S>
-cudaError_t launch_storage(const Launch &l)
-{
-    using T = typename Sto<S>::T;
-    const T *src = (const T *)l.src;
-    T *dst = (T *)l.dst;
-    if (l.kind == K_STEP) {
-        if (l.pattern == PAT_PULL) {
-            if (l.uout) {
-                // adjoint recompute: incompressible model only
-                return with_bool(l.force, [&](auto Fo) {
-                    k_step<L, S, PAT_PULL, false, decltype(Fo)::value, true>
-                        <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
-                    return cudaGetLastError();
-                });
-            }
-            return with_bool(l.comp, [&](auto C) {
-                return with_bool(l.force, [&](auto Fo) {
-                    k_step<L, S, PAT_PULL, decltype(C)::value, decltype(Fo)::value, false>
-                        <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
-                    return cudaGetLastError();
-                });
-            });
-        }
-        if (l.pattern == PAT_GATHER) {
-            return with_bool(l.comp, [&](auto C) {
-                return with_bool(l.force, [&](auto Fo) {
-                    k_step<L, S, PAT_GATHER, decltype(C)::value, decltype(Fo)::value, false>
-                        <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
-                    return cudaGetLastError();
-                });
-            });
-        }
-        return with_bool(l.comp, [&](auto C) {
-            return with_bool(l.force, [&](auto Fo) {
-                k_step<L, S, PAT_LOCAL, decltype(C)::value, decltype(Fo)::value, false>
-                    <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
-                return cudaGetLastError();
-            });
-        });
-    }
-    if (l.kind == K_INIT) {
-        return with_bool(l.pattern == 1, [&](auto AA) {
-            return with_bool(l.comp, [&](auto C) {
-                return with_bool(l.force, [&](auto Fo) {
-                    k_init<L, S, decltype(AA)::value, decltype(C)::value, decltype(Fo)::value>
-                        <<<l.grid, l.block, 0, l.stream>>>(dst, l.sp, l.p0, l.u0);
-                    return cudaGetLastError();
-                });
-            });
-        });
-    }
-    if (l.kind == K_MOMENTS) {
-        return with_bool(l.comp, [&](auto C) {
-            return with_bool(l.force, [&](auto Fo) {
-                constexpr bool c = decltype(C)::value, fo = decltype(Fo)::value;
-                switch (l.pattern) {
-                case FORM_LOCAL:
-                    k_moments<L, S, FORM_LOCAL, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, l.sp, l.mp);
-                    break;
-                case FORM_SWAPPED:
-                    k_moments<L, S, FORM_SWAPPED, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, l.sp, l.mp);
-                    break;
-                default:
-                    k_moments<L, S, FORM_STREAMED, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, l.sp, l.mp);
-                    break;
-                }
-                return cudaGetLastError();
-            });
-        });
-    }
-    return cudaErrorInvalidValue;
-}
-
-template <class L>
-cudaError_t launch_lattice(const Launch &l)
-{
-    switch (l.storage) {
-    case ST_F64:
-        return launch_storage<L, ST_F64>(l);
-    case ST_F32:
-        return launch_storage<L, ST_F32>(l);
-    case ST_F16S:
-        return launch_storage<L, ST_F16S>(l);
-    case ST_BF16S:
-        return launch_storage<L, ST_BF16S>(l);
-    }
-    return cudaErrorInvalidValue;
-}
 
 // Per-lattice entry points (one translation unit each).
 cudaError_t launch_d2q9(const Launch &l);

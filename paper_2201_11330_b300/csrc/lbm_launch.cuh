@@ -1,0 +1,124 @@
+// lbm_launch.cuh -- host-side dispatch from a Launch descriptor to the
+// template instantiation of each kernel (one translation unit per lattice).
+#pragma once
+
+#include "lbm_adjoint.cuh"
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+template <class F>
+inline cudaError_t with_bool(bool b, F &&f)
+{
+    return b ? f(std::true_type{}) : f(std::false_type{});
+}
+
+template <class L, int S>
+cudaError_t launch_storage(const Launch &l)
+{
+    using T = typename Sto<S>::T;
+    const T *src = (const T *)l.src;
+    T *dst = (T *)l.dst;
+    if (l.kind == K_STEP) {
+        if (l.pattern == PAT_PULL) {
+            if (l.uout) {
+                // adjoint recompute: incompressible model only
+                return with_bool(l.force, [&](auto Fo) {
+                    k_step<L, S, PAT_PULL, false, decltype(Fo)::value, true>
+                        <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                    return cudaGetLastError();
+                });
+            }
+            return with_bool(l.comp, [&](auto C) {
+                return with_bool(l.force, [&](auto Fo) {
+                    k_step<L, S, PAT_PULL, decltype(C)::value, decltype(Fo)::value, false>
+                        <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                    return cudaGetLastError();
+                });
+            });
+        }
+        if (l.pattern == PAT_GATHER) {
+            return with_bool(l.comp, [&](auto C) {
+                return with_bool(l.force, [&](auto Fo) {
+                    k_step<L, S, PAT_GATHER, decltype(C)::value, decltype(Fo)::value, false>
+                        <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                    return cudaGetLastError();
+                });
+            });
+        }
+        return with_bool(l.comp, [&](auto C) {
+            return with_bool(l.force, [&](auto Fo) {
+                k_step<L, S, PAT_LOCAL, decltype(C)::value, decltype(Fo)::value, false>
+                    <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                return cudaGetLastError();
+            });
+        });
+    }
+    if (l.kind == K_INIT) {
+        return with_bool(l.pattern == 1, [&](auto AA) {
+            return with_bool(l.comp, [&](auto C) {
+                return with_bool(l.force, [&](auto Fo) {
+                    k_init<L, S, decltype(AA)::value, decltype(C)::value, decltype(Fo)::value>
+                        <<<l.grid, l.block, 0, l.stream>>>(dst, l.sp, l.p0, l.u0);
+                    return cudaGetLastError();
+                });
+            });
+        });
+    }
+    if (l.kind == K_ADJ) {
+        using R = typename Sto<S>::R;
+        return with_bool(l.force, [&](auto Fo) {
+            k_adjoint<L, R, decltype(Fo)::value><<<l.grid, l.block, 0, l.stream>>>(l.sp, l.ap);
+            return cudaGetLastError();
+        });
+    }
+    if (l.kind == K_SEED) {
+        return with_bool(l.force, [&](auto Fo) {
+            k_adjoint_seed<L, S, decltype(Fo)::value><<<l.grid, l.block, 0, l.stream>>>(l.sp, l.ap);
+            return cudaGetLastError();
+        });
+    }
+    if (l.kind == K_FLUSH) {
+        using R = typename Sto<S>::R;
+        k_adjoint_flush<R><<<l.grid, l.block, 0, l.stream>>>((R *)l.ap.gF, l.ap.dJdF, l.count);
+        return cudaGetLastError();
+    }
+    if (l.kind == K_MOMENTS) {
+        return with_bool(l.comp, [&](auto C) {
+            return with_bool(l.force, [&](auto Fo) {
+                constexpr bool c = decltype(C)::value, fo = decltype(Fo)::value;
+                switch (l.pattern) {
+                case FORM_LOCAL:
+                    k_moments<L, S, FORM_LOCAL, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, l.sp, l.mp);
+                    break;
+                case FORM_SWAPPED:
+                    k_moments<L, S, FORM_SWAPPED, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, l.sp, l.mp);
+                    break;
+                default:
+                    k_moments<L, S, FORM_STREAMED, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, l.sp, l.mp);
+                    break;
+                }
+                return cudaGetLastError();
+            });
+        });
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class L>
+cudaError_t launch_lattice(const Launch &l)
+{
+    switch (l.storage) {
+    case ST_F64:
+        return launch_storage<L, ST_F64>(l);
+    case ST_F32:
+        return launch_storage<L, ST_F32>(l);
+    case ST_F16S:
+        return launch_storage<L, ST_F16S>(l);
+    case ST_BF16S:
+        return launch_storage<L, ST_BF16S>(l);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lbm
