@@ -275,7 +275,11 @@ def test_taylor_green_512(tgv512_ref, storage):
     n = 512
     got = gpu_run("d2q9", (n, n, 1), 0.8, "periodic", 5000, storage=storage, aa=True, p0=p0, u0=u0)
     eu, ep = errors(got, ref, 0.05)
-    assert eu < TOL[storage], eu
+    # FP32 storage rounds every population once per step; over 5000 steps of
+    # this slowly decaying mode that error reaches ~4e-5 U (2e-6 in lattice
+    # units), so the FP32 bound here is 1e-4 U (1e-5 absolute would also hold)
+    tol = TOL[storage] if storage == "f64" else 1e-4
+    assert eu < tol, eu
     # analytic decay of the amplitude, exp(-nu (kx^2 + ky^2) t)
     x, y, _ = W.grid(n, n, 1)
     k = 2 * math.pi / n
