@@ -167,6 +167,43 @@ int lbm_adjoint_backward(lbm_ctx *ctx, void *adj_workspace, size_t bytes, double
 int lbm_adjoint(lbm_ctx *ctx, int64_t T, int64_t K, void *adj_workspace, size_t bytes,
                 double *J, double *dJdF, double *dJdU);
 
+/* Allocation-free monitor reduction (the paper has no counterpart).
+ *
+ * Same six values as lbm_reduce, computed from a distribution buffer the
+ * caller passes, for callers that hold such a buffer (for example a
+ * checkpoint from lbm_get_state) but may not allocate device memory: code
+ * running under an allocator that is frozen after start-up, inside a host
+ * callback, or a tool that only inspects buffers it is handed.  It needs no
+ * context and no workspace, and calls no cudaMalloc/cudaFree or other
+ * allocating routine.
+ *
+ * Scratch: a fixed device array inside the library holding
+ * LBM_NOALLOC_MAX_PARTIALS partial sums (8 doubles each) plus the result,
+ * about 512 KB, present on every GPU that loads the library until the
+ * process exits.  The call needs ceil(nx/256) * nz partials (x-segments of
+ * at most 256 nodes times z-planes) and returns LBM_ERR_NOMEM, launching
+ * nothing, when that exceeds LBM_NOALLOC_MAX_PARTIALS.  Every partial is
+ * rewritten by each call, so nothing needs clearing; but all calls on a
+ * device share the array, so calls that overlap on the GPU (different
+ * streams or threads) race and must be serialised by the caller.  The
+ * first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture.
+ *
+ * Arguments: lattice, nx, ny, nz, bc and *opts as given to lbm_create for
+ * the context that produced the buffer; state: device buffer of
+ * lbm_state_bytes() bytes in that context's layout; step: the step count
+ * lbm_get_state reported (it selects the AA layout); force: the device FP32
+ * force field (d*N) the context used, or NULL; cuda_stream: stream to run
+ * on (NULL = default); out: host, 6 doubles as for lbm_reduce.
+ * Synchronises the stream.  Errors: LBM_ERR_ARG (bad arguments),
+ * LBM_ERR_NOMEM (scratch too small for the shape), LBM_ERR_CUDA,
+ * LBM_ERR_UNSTABLE (a non-finite result). */
+#define LBM_NOALLOC_MAX_PARTIALS 8192
+int lbm_reduce_state_noalloc(int lattice, int nx, int ny, int nz, int bc, const lbm_opts *opts,
+                             const void *state, int64_t step, const float *force,
+                             void *cuda_stream, double *out);
+
 /* Static description of a status code. */
 const char *lbm_error_string(int status);
 

@@ -35,7 +35,8 @@ EXPORTS = [
     "lbm_set_stream", "lbm_init", "lbm_set_force", "lbm_set_lid", "lbm_step",
     "lbm_step_count", "lbm_macroscopic", "lbm_reduce", "lbm_state_bytes", "lbm_get_state",
     "lbm_set_state", "lbm_adjoint_workspace_bytes", "lbm_adjoint_forward",
-    "lbm_adjoint_backward", "lbm_adjoint", "lbm_error_string", "lbm_destroy",
+    "lbm_adjoint_backward", "lbm_adjoint", "lbm_reduce_state_noalloc", "lbm_error_string",
+    "lbm_destroy",
 ]
 
 
@@ -90,6 +91,7 @@ def load():
         "lbm_adjoint_forward": (ip, [_vp, _i64, _i64, _vp, _sz, _dp]),
         "lbm_adjoint_backward": (ip, [_vp, _vp, _sz, _vp, _dp]),
         "lbm_adjoint": (ip, [_vp, _i64, _i64, _vp, _sz, _dp, _vp, _dp]),
+        "lbm_reduce_state_noalloc": (ip, [ip, ip, ip, ip, ip, op, _vp, _i64, _vp, _vp, _dp]),
         "lbm_error_string": (ctypes.c_char_p, [ip]),
         "lbm_destroy": (None, [_vp]),
     }
@@ -197,6 +199,17 @@ def lbm_adjoint(ctx, T, K, ws_ptr, nbytes, dJdF_ptr):
     _check(load().lbm_adjoint(ctx, int(T), int(K), ws_ptr, nbytes, ctypes.byref(J), dJdF_ptr, gU),
            "lbm_adjoint")
     return J.value, list(gU)
+
+
+def lbm_reduce_state_noalloc(lattice, nx, ny, nz, bc, opts, state_ptr, step, force_ptr,
+                             stream_ptr):
+    """Monitor reduction of a state buffer without any device allocation
+    (for callers that may not allocate; see include/lbm.h)."""
+    out = (ctypes.c_double * 6)()
+    _check(load().lbm_reduce_state_noalloc(lattice, nx, ny, nz, bc, ctypes.byref(opts), state_ptr,
+                                           int(step), force_ptr, stream_ptr, out),
+           "lbm_reduce_state_noalloc")
+    return list(out)
 
 
 def lbm_error_string(status: int) -> str:
