@@ -374,7 +374,10 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--size", type=int, default=HEADLINE["n"])
+    ap.add_argument("--size", type=int, default=HEADLINE["n"],
+                    help="cavity side of the headline run (profiling uses smaller boxes)")
+    ap.add_argument("--storage", default=HEADLINE["storage"], choices=list(BYTES_OF),
+                    help="storage of the headline run (profiling of the other variants)")
     ap.add_argument("--no-extras", action="store_true",
                     help="headline line only (no storage variants, D3Q27, adjoint, CPU)")
     args = ap.parse_args()
@@ -399,6 +402,7 @@ def main():
 
     hb = dict(HEADLINE)
     hb["n"] = args.size
+    hb["storage"] = args.storage
     peak, peak_kind = load_peaks()
 
     # headline, with clocks sampled during its timed region
@@ -411,10 +415,11 @@ def main():
     N = head["nodes"]
     bpn = head["bytes_per_node"]
     dom_ms = max(head["gather_ms"], head["local_ms"])
-    dom_name = "k_step<D3Q19,F32,GATHER>" if head["gather_ms"] >= head["local_ms"] else \
-        "k_step<D3Q19,F32,LOCAL>"
+    st_tag = hb["storage"].upper()
+    gather_dom = head["gather_ms"] >= head["local_ms"]
+    dom_name = f"k_step<D3Q19,{st_tag},{'GATHER' if gather_dom else 'LOCAL'}>"
     achieved = N * bpn / (dom_ms * 1e-3) / 1e9
-    traffic = load_traffic("d3q19_f32_gather")
+    traffic = load_traffic(f"d3q19_{hb['storage']}_{'gather' if gather_dom else 'local'}_{hb['n']}")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": dom_name, "peak_kind": f"{peak_kind} copy bandwidth",
@@ -451,7 +456,8 @@ def main():
         line = {
             "metric": METRIC, "value": head["glups"], "unit": "GLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if hb["storage"] == "f64" else "f32",
             "data": "synthetic",
             "config": {"workload": workload_name(hb["lattice"], hb["n"], hb["re"], hb["storage"],
                                                  hb["aa"]),
