@@ -43,16 +43,18 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, out: str = LIB, build_dir: str = BUILD,
+          defines=()) -> str:
+    """Compile every csrc/*.cu and link `out` (defines: extra -D flags)."""
+    if not force and out == LIB and up_to_date():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
     procs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         log = open(obj + ".log", "w")
-        cmd = [nvcc, *NVCC_FLAGS, *ARCH, "-c", src, "-o", obj]
+        cmd = [nvcc, *NVCC_FLAGS, *[f"-D{d}" for d in defines], *ARCH, "-c", src, "-o", obj]
         procs.append((src, obj, log, subprocess.Popen(cmd, stdout=log, stderr=subprocess.STDOUT)))
     failed = []
     for src, obj, log, p in procs:
@@ -60,21 +62,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
         log.close()
         if p.returncode != 0:
             failed.append(src)
-    with open(os.path.join(BUILD, "ptxas.log"), "w") as out:
+    with open(os.path.join(build_dir, "ptxas.log"), "w") as fh:
         for src, obj, _, _ in procs:
-            out.write(open(obj + ".log").read())
+            fh.write(open(obj + ".log").read())
     if failed:
         for src in failed:
-            obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+            obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
             sys.stderr.write(open(obj + ".log").read()[-4000:])
         raise RuntimeError(f"nvcc failed for {failed}")
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in sources()]
-    tmp = LIB + ".tmp"
+    objs = [os.path.join(build_dir, os.path.basename(s)[:-3] + ".o") for s in sources()]
+    tmp = out + ".tmp"
     subprocess.check_call([nvcc, "-shared", *ARCH, "-o", tmp, *objs])
-    os.replace(tmp, LIB)
+    os.replace(tmp, out)
     if verbose:
-        print("built", LIB)
-    return LIB
+        print("built", out)
+    return out
 
 
 if __name__ == "__main__":

@@ -8,6 +8,7 @@
 #include <new>
 
 #include "lbm.h"
+#include "lbm_bulk.cuh"
 #include "lbm_capi_internal.h"
 #include "lbm_kernels.cuh"
 
@@ -140,6 +141,24 @@ void fill_params(lbm_ctx *c)
     p.u_out = nullptr;
 }
 
+// The staged kernel copies whole 16-byte aligned row segments: nx (hence N)
+// must be a multiple of 16 bytes' worth of values.
+bool bulk_eligible(const lbm_ctx *c)
+{
+    const int per16 = 16 / (int)storage_elem(c->opts.storage);
+    return c->nx % per16 == 0;
+}
+
+bool use_bulk(const lbm_ctx *c)
+{
+    if (c->kernel_variant == LBM_KERNEL_PLAIN || !bulk_eligible(c))
+        return false;
+    if (c->kernel_variant == LBM_KERNEL_STAGED)
+        return true;
+    // automatic choice: the plain kernel, measured faster for every storage
+    return false;
+}
+
 Launch base_launch(const lbm_ctx *c, int kind)
 {
     Launch l;
@@ -174,6 +193,19 @@ int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u
     if (u_out) {
         l.uout = true;
         l.sp.u_out = u_out;
+    } else if (use_bulk(c)) {
+        if (c->num_sms <= 0) {
+            int dev = 0, nsm = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return LBM_ERR_CUDA;
+            c->num_sms = nsm;
+        }
+        l.bulk = true;
+        l.bulk_xseg = (c->nx + kBulkSeg - 1) / kBulkSeg;
+        l.bulk_nseg = l.bulk_xseg * c->ny * c->nz;
+        l.num_sms = c->num_sms;
+        l.err = c->err;
     }
     return dispatch(c->lattice, l) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
@@ -285,6 +317,9 @@ int lbm_create(int lattice, int nx, int ny, int nz, double tau, int bc, const lb
     c->step = 0;
     c->bx = default_block(nx);
     c->initialized = false;
+    c->kernel_variant = LBM_KERNEL_AUTO;
+    c->num_sms = 0;
+    c->err = (unsigned *)((char *)c->result + 64);
     fill_params(c);
     *out = c;
     return LBM_OK;
@@ -309,6 +344,8 @@ int lbm_init(lbm_ctx *c, const double *p, const double *u)
     c->cur = 0;
     l.dst = c->f[0];
     c->step = 0;
+    if (cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
     if (dispatch(c->lattice, l) != cudaSuccess)
         return LBM_ERR_CUDA;
     c->initialized = true;
@@ -366,6 +403,23 @@ int lbm_step(lbm_ctx *c, int64_t n)
 
 int64_t lbm_step_count(const lbm_ctx *c) { return c ? c->step : -1; }
 
+int lbm_set_kernel_variant(lbm_ctx *c, int variant)
+{
+    if (!c || variant < LBM_KERNEL_AUTO || variant > LBM_KERNEL_STAGED)
+        return LBM_ERR_ARG;
+    if (variant == LBM_KERNEL_STAGED && !bulk_eligible(c))
+        return LBM_ERR_ARG;
+    c->kernel_variant = variant;
+    return LBM_OK;
+}
+
+int lbm_kernel_variant_in_use(const lbm_ctx *c)
+{
+    if (!c)
+        return LBM_ERR_ARG;
+    return use_bulk(c) ? LBM_KERNEL_STAGED : LBM_KERNEL_PLAIN;
+}
+
 int lbm_macroscopic(lbm_ctx *c, void *p_out, void *u_out, int out_dtype)
 {
     if (!c || (out_dtype != 0 && out_dtype != 1))
@@ -390,11 +444,15 @@ int lbm_reduce(lbm_ctx *c, double *out)
         return rc;
     if (launch_finish(c->partials, c->nred, c->result, c->stream) != cudaSuccess)
         return LBM_ERR_CUDA;
-    double r[kReduceVals];
+    double r[12];  // the six values, padding, the error word at byte 64
     if (cudaMemcpyAsync(r, c->result, sizeof(r), cudaMemcpyDeviceToHost, c->stream) !=
         cudaSuccess)
         return LBM_ERR_CUDA;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    unsigned errword;
+    memcpy(&errword, (const char *)r + 64, sizeof(errword));
+    if (errword != 0)
         return LBM_ERR_CUDA;
     out[0] = r[0] + (c->shifted ? (double)c->N : 0.0);
     out[1] = r[1];

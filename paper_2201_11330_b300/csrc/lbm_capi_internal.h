@@ -29,6 +29,9 @@ struct lbm_ctx {
     int64_t step;
     int bx;  // threads per block along x
     bool initialized;
+    int kernel_variant;  // lbm_kernel_variant
+    int num_sms;         // queried at the first staged launch
+    unsigned *err;       // error word of the bounded waits (in the workspace)
     lbm::StepParams sp;
     // adjoint run recorded by lbm_adjoint_forward for lbm_adjoint_backward
     int64_t adj_T, adj_K;

@@ -88,6 +88,19 @@ __device__ __forceinline__ void st(T *p, T v)
 #endif
 }
 
+// ---- explicitly rounded arithmetic ------------------------------------------
+// The collision is inlined into several kernels (pull, AA halves, staged); to
+// make all of them round identically, every multiply-add is written out: the
+// _rn intrinsics are never fused or split by the compiler.
+__device__ __forceinline__ float o_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float o_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float o_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float o_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double o_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double o_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double o_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double o_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // ---- collision (Sec. 2.1) ---------------------------------------------------
 // g holds the populations (shifted by sigma*t_a when the storage is shifted);
 // on return it holds the post-collision populations in the same shift.  The
@@ -105,25 +118,25 @@ __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coe
     R sp[H], sm[H];
     SFor<0, H>::run([&](auto A_) {
         constexpr int a = decltype(A_)::value;
-        sp[a] = g[a] + g[opp<L>(a)];
-        sm[a] = g[a] - g[opp<L>(a)];
+        sp[a] = o_add(g[a], g[opp<L>(a)]);
+        sm[a] = o_sub(g[a], g[opp<L>(a)]);
     });
     R s = g[H];
     R j[3] = {R(0), R(0), R(0)};
     SFor<0, H>::run([&](auto A_) {
         constexpr int a = decltype(A_)::value;
-        s += sp[a];
+        s = o_add(s, sp[a]);
         SFor<0, 3>::run([&](auto K_) {
             constexpr int k = decltype(K_)::value;
             if constexpr (L::e(a, k) == 1)
-                j[k] += sm[a];
+                j[k] = o_add(j[k], sm[a]);
             else if constexpr (L::e(a, k) == -1)
-                j[k] -= sm[a];
+                j[k] = o_sub(j[k], sm[a]);
         });
     });
     R rho, ir;
     if constexpr (COMP) {
-        rho = s + c.sigma;
+        rho = o_add(s, c.sigma);
         ir = R(1) / rho;
     } else {
         rho = c.rho0;
@@ -132,18 +145,17 @@ __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coe
     SFor<0, 3>::run([&](auto K_) {
         constexpr int k = decltype(K_)::value;
         if constexpr (FORCE)
-            u[k] = (j[k] + R(0.5) * F[k]) * ir;
+            u[k] = o_mul(o_fma(R(0.5), F[k], j[k]), ir);
         else
-            u[k] = j[k] * ir;
+            u[k] = o_mul(j[k], ir);
     });
-    const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    R A = s - R(1.5) * rho * uu;
-    R uF = R(0);
+    const R uu = o_fma(u[2], u[2], o_fma(u[1], u[1], o_mul(u[0], u[0])));
+    R A = o_fma(o_mul(R(-1.5), rho), uu, s);
     if constexpr (FORCE) {
-        uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
-        A -= R(3) * c.kf * uF;
+        const R uF = o_fma(u[2], F[2], o_fma(u[1], F[1], o_mul(u[0], F[0])));
+        A = o_fma(o_mul(R(-3), c.kf), uF, A);
     }
-    const R r3 = R(3) * rho, r45 = R(4.5) * rho;
+    const R r3 = o_mul(R(3), rho), r45 = o_mul(R(4.5), rho);
     const R om = c.omega;
     SFor<0, H>::run([&](auto A_) {
         constexpr int a = decltype(A_)::value;
@@ -154,30 +166,30 @@ __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coe
         SFor<0, 3>::run([&](auto K_) {
             constexpr int k = decltype(K_)::value;
             if constexpr (L::e(a, k) == 1) {
-                eu += u[k];
+                eu = o_add(eu, u[k]);
                 if constexpr (FORCE)
-                    eF += F[k];
+                    eF = o_add(eF, F[k]);
             } else if constexpr (L::e(a, k) == -1) {
-                eu -= u[k];
+                eu = o_sub(eu, u[k]);
                 if constexpr (FORCE)
-                    eF -= F[k];
+                    eF = o_sub(eF, F[k]);
             }
         });
-        R sym = A + r45 * eu * eu;
-        R asym = r3 * eu;
+        R sym = o_fma(o_mul(r45, eu), eu, A);
+        R asym = o_mul(r3, eu);
         if constexpr (FORCE) {
-            sym += R(9) * c.kf * eu * eF;
-            asym += R(3) * c.kf * eF;
+            sym = o_fma(o_mul(o_mul(R(9), c.kf), eu), eF, sym);
+            asym = o_fma(o_mul(R(3), c.kf), eF, asym);
         }
-        sym *= t;
-        asym *= t;
-        const R fa = sym + asym, fb = sym - asym;
-        g[a] = g[a] + om * (fa - g[a]);
-        g[b] = g[b] + om * (fb - g[b]);
+        sym = o_mul(sym, t);
+        asym = o_mul(asym, t);
+        const R fa = o_add(sym, asym), fb = o_sub(sym, asym);
+        g[a] = o_fma(om, o_sub(fa, g[a]), g[a]);
+        g[b] = o_fma(om, o_sub(fb, g[b]), g[b]);
     });
     {
         const R t0 = R(L::w(H));
-        g[H] = g[H] + om * (t0 * A - g[H]);
+        g[H] = o_fma(om, o_sub(o_mul(t0, A), g[H]), g[H]);
     }
 }
 
@@ -269,6 +281,8 @@ __device__ __forceinline__ void make_axes(const StepParams &p, int x, int y, int
 }
 
 // ---- one node of one time step ----------------------------------------------
+// INTERIOR: the node's row has neighbours inside the box in y and z (no wall,
+// no wrap), so only the x axis needs per-thread boundary logic.
 template <class L, int S, int PAT, bool COMP, bool FORCE, bool UOUT, bool INTERIOR>
 __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typename Sto<S>::T *dst,
                                           const StepParams &p, int x, int y, int z)
@@ -359,6 +373,9 @@ __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typenam
 
 // grid: (ceil(nx/blockDim.x), ny, nz); one node per thread.
 template <class L, int S, int PAT, bool COMP, bool FORCE, bool UOUT>
+// (__launch_bounds__ with an explicit minimum of 1 block lets nvcc roughly
+// double the register count of these kernels and halves their occupancy;
+// the thread bound alone keeps them at 40-48 registers.)
 __global__ void __launch_bounds__(256) k_step(const typename Sto<S>::T *src,
                                               typename Sto<S>::T *dst, const StepParams p)
 {
@@ -394,36 +411,39 @@ __global__ void __launch_bounds__(256) k_init(typename Sto<S>::T *dst, const Ste
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= p.nx)
         return;
+    using R = typename Sto<S>::R;
     const size_t N = (size_t)p.N;
     const int n = x + p.nx * (y + p.ny * z);
-    const Coef<double> &c = p.cd;
+    const Coef<R> &c = coef<R>(p);
+    // shifted pressure P - sigma taken in FP64 before rounding to R
     const double P = p0 ? 3.0 * p0[n] : 1.0;
-    double u[3] = {0.0, 0.0, 0.0};
+    const R dP = R(P - double(c.sigma));
+    R u[3] = {R(0), R(0), R(0)};
     if (u0)
         for (int k = 0; k < L::D; ++k)
-            u[k] = u0[k * N + n];
-    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    double g[Q];
+            u[k] = R(u0[k * N + n]);
+    const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const R rho = COMP ? R(P) : c.rho0;
+    R g[Q];
     SFor<0, Q>::run([&](auto A_) {
         constexpr int a = decltype(A_)::value;
-        const double t = L::w(a);
-        const double eu = L::e(a, 0) * u[0] + L::e(a, 1) * u[1] + L::e(a, 2) * u[2];
-        const double poly = 3.0 * eu + 4.5 * eu * eu - 1.5 * uu;
-        const double feq = COMP ? t * P * (1.0 + poly) : t * (P + c.rho0 * poly);
-        g[a] = feq - c.sigma * t;
+        const R t = R(L::w(a));
+        const R eu = R(L::e(a, 0)) * u[0] + R(L::e(a, 1)) * u[1] + R(L::e(a, 2)) * u[2];
+        const R poly = R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu;
+        // feq - sigma t = t [(P - sigma) + rho poly]  (Eq. (incompressible_feq) / Eq. (feq))
+        g[a] = t * (dP + rho * poly);
     });
     if constexpr (FORCE) {
-        double F[3] = {0.0, 0.0, 0.0};
+        R F[3] = {R(0), R(0), R(0)};
         for (int k = 0; k < L::D; ++k)
-            F[k] = p.F[k * N + n];
-        double uc[3];
-        collide<L, double, COMP, true>(g, F, c, uc);
+            F[k] = R(p.F[k * N + n]);
+        R uc[3];
+        collide<L, R, COMP, true>(g, F, c, uc);
     }
     SFor<0, Q>::run([&](auto A_) {
         constexpr int a = decltype(A_)::value;
-        using R = typename Sto<S>::R;
         const int slot = AA ? opp<L>(a) : a;
-        dst[slot * N + n] = Sto<S>::enc(R(g[a]));
+        dst[slot * N + n] = Sto<S>::enc(g[a]);
     });
 }
 
@@ -506,28 +526,28 @@ __global__ void __launch_bounds__(256) k_moments(const typename Sto<S>::T *src, 
             R s = R(0), j[3] = {R(0), R(0), R(0)};
             SFor<0, Q>::run([&](auto A_) {
                 constexpr int a = decltype(A_)::value;
-                s += g[a];
+                s = o_add(s, g[a]);
                 SFor<0, 3>::run([&](auto K_) {
                     constexpr int k = decltype(K_)::value;
                     if constexpr (L::e(a, k) == 1)
-                        j[k] += g[a];
+                        j[k] = o_add(j[k], g[a]);
                     else if constexpr (L::e(a, k) == -1)
-                        j[k] -= g[a];
+                        j[k] = o_sub(j[k], g[a]);
                 });
             });
             // post-collision state: j* = j + F, so u = (j* - F/2)/rho
-            const R rho = COMP ? s + c.sigma : c.rho0;
+            const R rho = COMP ? o_add(s, c.sigma) : c.rho0;
             const R ir = COMP ? R(1) / rho : c.inv_rho0;
             R u[3];
             for (int k = 0; k < 3; ++k) {
                 R jk = j[k];
                 if constexpr (FORCE) {
                     if (k < L::D)
-                        jk -= R(0.5) * R(p.F[k * N + n]);
+                        jk = o_fma(R(-0.5), R(p.F[k * N + n]), jk);
                 }
-                u[k] = jk * ir;
+                u[k] = o_mul(jk, ir);
             }
-            const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            const R uu = o_fma(u[2], u[2], o_fma(u[1], u[1], o_mul(u[0], u[0])));
             if (m.p_out) {
                 const R pv = (s + c.sigma) * R(1.0 / 3.0);
                 if (m.out_f32)
@@ -630,6 +650,9 @@ struct Launch {
     MomParams mp;
     AdjParams ap;
     size_t count;  // K_FLUSH
+    bool bulk;     // K_STEP: use the shared-memory staged kernel (lbm_bulk.cuh)
+    int bulk_nseg, bulk_xseg, num_sms;
+    unsigned *err;  // error word for bounded waits
     dim3 grid, block;
     cudaStream_t stream;
 };

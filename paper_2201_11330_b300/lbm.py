@@ -23,6 +23,8 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_STATE, LBM_ERR_NOME
 LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 = 0, 1, 2
 LBM_BC_PERIODIC, LBM_BC_CAVITY, LBM_BC_CHANNEL = 0, 1, 2
 LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = 0, 1, 2, 3
+LBM_KERNEL_AUTO, LBM_KERNEL_PLAIN, LBM_KERNEL_STAGED = 0, 1, 2
+KERNELS = {"auto": LBM_KERNEL_AUTO, "plain": LBM_KERNEL_PLAIN, "staged": LBM_KERNEL_STAGED}
 
 LATTICES = {"d2q9": LBM_D2Q9, "d3q19": LBM_D3Q19, "d3q27": LBM_D3Q27}
 BCS = {"periodic": LBM_BC_PERIODIC, "cavity": LBM_BC_CAVITY, "channel": LBM_BC_CHANNEL}
@@ -33,7 +35,7 @@ QD = {LBM_D2Q9: (9, 2), LBM_D3Q19: (19, 3), LBM_D3Q27: (27, 3)}
 EXPORTS = [
     "lbm_default_opts", "lbm_tau_from_paper", "lbm_workspace_bytes", "lbm_create",
     "lbm_set_stream", "lbm_init", "lbm_set_force", "lbm_set_lid", "lbm_step",
-    "lbm_step_count", "lbm_macroscopic", "lbm_reduce", "lbm_state_bytes", "lbm_get_state",
+    "lbm_step_count", "lbm_set_kernel_variant", "lbm_kernel_variant_in_use", "lbm_macroscopic", "lbm_reduce", "lbm_state_bytes", "lbm_get_state",
     "lbm_set_state", "lbm_adjoint_workspace_bytes", "lbm_adjoint_forward",
     "lbm_adjoint_backward", "lbm_adjoint", "lbm_reduce_state_noalloc", "lbm_error_string",
     "lbm_destroy",
@@ -82,6 +84,8 @@ def load():
         "lbm_set_lid": (ip, [_vp, _dp]),
         "lbm_step": (ip, [_vp, _i64]),
         "lbm_step_count": (_i64, [_vp]),
+        "lbm_set_kernel_variant": (ip, [_vp, ip]),
+        "lbm_kernel_variant_in_use": (ip, [_vp]),
         "lbm_macroscopic": (ip, [_vp, _vp, _vp, ip]),
         "lbm_reduce": (ip, [_vp, _dp]),
         "lbm_state_bytes": (_sz, [_vp]),
@@ -150,6 +154,14 @@ def lbm_step(ctx, n: int):
 
 def lbm_step_count(ctx) -> int:
     return load().lbm_step_count(ctx)
+
+
+def lbm_set_kernel_variant(ctx, variant: int):
+    _check(load().lbm_set_kernel_variant(ctx, int(variant)), "lbm_set_kernel_variant")
+
+
+def lbm_kernel_variant_in_use(ctx) -> int:
+    return load().lbm_kernel_variant_in_use(ctx)
 
 
 def lbm_macroscopic(ctx, p_ptr, u_ptr, out_dtype: int):
@@ -241,7 +253,7 @@ class Lattice:
 
     def __init__(self, lattice, nx, ny, nz, tau, bc, *, storage="f32", aa=False,
                  compressible=False, f32_unshifted=False, rho0=1.0, lid=(0.0, 0.0, 0.0),
-                 has_force=False, device="cuda"):
+                 has_force=False, kernel="auto", device="cuda"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the LBM library needs a CUDA device")
@@ -272,6 +284,8 @@ class Lattice:
                               self.workspace.data_ptr(), nbytes, self._stream())
         self._force = None
         self._adj_ws = None
+        if kernel != "auto":
+            self.set_kernel(kernel)
 
     def _stream(self):
         return self.torch.cuda.current_stream(self.device).cuda_stream
@@ -322,6 +336,16 @@ class Lattice:
     @property
     def step_count(self):
         return lbm_step_count(self.ctx)
+
+    def set_kernel(self, variant):
+        """'auto', 'plain' or 'staged' (see lbm_set_kernel_variant)."""
+        lbm_set_kernel_variant(self.ctx, _key(KERNELS, variant))
+        return self
+
+    @property
+    def kernel(self):
+        v = lbm_kernel_variant_in_use(self.ctx)
+        return {LBM_KERNEL_PLAIN: "plain", LBM_KERNEL_STAGED: "staged"}[v]
 
     def macroscopic(self, dtype=None):
         """(p (N,), u (d, N)) of the current step."""

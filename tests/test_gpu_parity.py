@@ -290,3 +290,64 @@ def test_taylor_green_512(tgv512_ref, storage):
     lat = got[2]
     r = lat.reduce()
     assert abs(r["mass"] - 3 * p0.sum()) <= (1e-12 if storage == "f64" else 1e-6) * n * n
+
+
+# ---------------------------------------------------------------------------
+# The shared-memory staged kernel (bulk asynchronous copies) against the
+# plain kernel: same arithmetic and the same loaded values, so bitwise equal.
+
+
+STAGED_SHAPES = [("d3q19", (520, 9, 7)), ("d3q19", (48, 13, 11)), ("d3q27", (264, 7, 6)),
+                 ("d2q9", (304, 37, 1)), ("d3q19", (16, 1, 3)), ("d3q27", (8, 3, 3))]
+
+
+def _staged_run(lattice, shape, bc, storage, aa, steps, kernel, force):
+    from paper_2201_11330_b300.lbm import Lattice
+    Q, d = oracle.dims(lattice)
+    p0, u0 = W.random_smooth_state(*shape, d, amp_u=0.04, seed=44)
+    lat = Lattice(lattice, *shape, 0.6, bc, storage=storage, aa=aa, kernel=kernel,
+                  lid=(0.07, 0.0, 0.01) if bc != "periodic" else (0, 0, 0), has_force=force)
+    if force:
+        lat.set_force(torch.from_numpy(W.fourier_force(*shape, amplitude=2e-5, seed=8,
+                                                       dims=d)).cuda())
+    lat.init(torch.from_numpy(p0).cuda(), torch.from_numpy(u0).cuda())
+    lat.step(steps)
+    assert lat.kernel == kernel
+    p, u = lat.macroscopic()
+    return p.cpu().numpy(), u.cpu().numpy()
+
+
+@pytest.mark.parametrize("lattice,shape", STAGED_SHAPES)
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s", "bf16s"])
+@pytest.mark.parametrize("bc", ["cavity", "periodic", "channel"])
+def test_staged_equals_plain_bitwise(lattice, shape, storage, bc):
+    per16 = {"f64": 2, "f32": 4, "f16s": 8, "bf16s": 8}[storage]
+    if shape[0] % per16:
+        pytest.skip("shape not eligible for the staged kernel")
+    for aa, steps, force in ((False, 9, True), (True, 9, False), (True, 10, True)):
+        a = _staged_run(lattice, shape, bc, storage, aa, steps, "plain", force)
+        b = _staged_run(lattice, shape, bc, storage, aa, steps, "staged", force)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), (aa, steps)
+
+
+@pytest.mark.parametrize("lattice,shape,bc", [("d3q19", (40, 29, 23), "cavity"),
+                                              ("d3q27", (264, 9, 7), "channel"),
+                                              ("d2q9", (304, 67, 1), "periodic")])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_staged_parity_with_oracle(lattice, shape, bc, storage):
+    Q, d = oracle.dims(lattice)
+    p0, u0 = W.random_smooth_state(*shape, d, amp_u=0.04, amp_p=2e-3, seed=21)
+    lid = (0.08, 0.0, 0.02) if bc != "periodic" else None
+    F = W.fourier_force(*shape, amplitude=2e-5, seed=5, dims=d)
+    ref = oracle_run(lattice, shape, 0.62, bc, 61, lid=lid, F=F, p0=p0, u0=u0)
+    from paper_2201_11330_b300.lbm import Lattice
+    for aa in (False, True):
+        lat = Lattice(lattice, *shape, 0.62, bc, storage=storage, aa=aa, kernel="staged",
+                      lid=lid or (0, 0, 0), has_force=True)
+        lat.set_force(torch.from_numpy(F).cuda())
+        lat.init(torch.from_numpy(p0).cuda(), torch.from_numpy(u0).cuda())
+        lat.step(61)
+        p, u = lat.macroscopic()
+        eu, ep = errors((p.cpu().numpy(), u.cpu().numpy()), ref, 0.05)
+        assert eu < TOL[storage] and ep < 10 * TOL[storage], (aa, eu, ep)
+        assert lat.reduce()["mass"] > 0  # also checks the staged kernel's error word
