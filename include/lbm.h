@@ -131,22 +131,31 @@ int lbm_step(lbm_ctx *ctx, int64_t n);
 /* Steps taken since lbm_init (or the value given to lbm_set_state). */
 int64_t lbm_step_count(const lbm_ctx *ctx);
 
-/* Which kernel runs the step (both compute the same arithmetic and give
+/* Which kernel runs the step (all compute the same arithmetic and give
  * bitwise identical results):
- *   LBM_KERNEL_PLAIN  every thread loads its Q populations straight from HBM;
+ *   LBM_KERNEL_PLAIN  one node per thread, Q populations straight from HBM;
  *   LBM_KERNEL_STAGED persistent blocks stage whole row segments of every
  *                     direction in shared memory with bulk asynchronous copies
  *                     (cp.async.bulk + mbarrier, several segments in flight);
  *                     needs nx to be a multiple of 16 bytes' worth of values
  *                     (8 for 16-bit storage, 4 for FP32, 2 for FP64);
- *   LBM_KERNEL_AUTO   the library's measured choice for the storage type.
+ *   LBM_KERNEL_PAIRED 16-bit storage only, nx even: two adjacent nodes per
+ *                     thread, one 32-bit word per slot, e_x = +-1 directions
+ *                     realigned with warp shuffles;
+ *   LBM_KERNEL_AUTO   the library's measured choice for the storage type
+ *                     (PAIRED where eligible, else PLAIN).
  * The adjoint's recompute always uses the plain kernel.  LBM_ERR_ARG for an
  * unknown variant or STAGED on an ineligible shape.  A bounded wait of the
  * staged kernel that times out is reported by the next lbm_reduce as
  * LBM_ERR_CUDA. */
-typedef enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_PLAIN = 1, LBM_KERNEL_STAGED = 2 } lbm_kernel_variant;
+typedef enum {
+    LBM_KERNEL_AUTO = 0,
+    LBM_KERNEL_PLAIN = 1,
+    LBM_KERNEL_STAGED = 2,
+    LBM_KERNEL_PAIRED = 3
+} lbm_kernel_variant;
 int lbm_set_kernel_variant(lbm_ctx *ctx, int variant);
-/* The variant lbm_step currently launches (LBM_KERNEL_PLAIN or _STAGED). */
+/* The variant lbm_step currently launches (PLAIN, STAGED or PAIRED). */
 int lbm_kernel_variant_in_use(const lbm_ctx *ctx);
 
 /* Sec. 3.4 PostProcessing: p = c_s^2 sum f and u = (sum e f + F/2)/rho of

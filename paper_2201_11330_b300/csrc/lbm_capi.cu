@@ -149,14 +149,23 @@ bool bulk_eligible(const lbm_ctx *c)
     return c->nx % per16 == 0;
 }
 
+// The paired kernel moves two 16-bit values per thread and slot.
+bool pair_eligible(const lbm_ctx *c)
+{
+    return (c->opts.storage == LBM_F16S || c->opts.storage == LBM_BF16S) && c->nx % 2 == 0;
+}
+
 bool use_bulk(const lbm_ctx *c)
 {
-    if (c->kernel_variant == LBM_KERNEL_PLAIN || !bulk_eligible(c))
+    return c->kernel_variant == LBM_KERNEL_STAGED && bulk_eligible(c);
+}
+
+bool use_pair(const lbm_ctx *c)
+{
+    if (!pair_eligible(c))
         return false;
-    if (c->kernel_variant == LBM_KERNEL_STAGED)
-        return true;
-    // automatic choice: the plain kernel, measured faster for every storage
-    return false;
+    // automatic choice (measured): paired for 16-bit storage
+    return c->kernel_variant == LBM_KERNEL_PAIRED || c->kernel_variant == LBM_KERNEL_AUTO;
 }
 
 Launch base_launch(const lbm_ctx *c, int kind)
@@ -193,6 +202,8 @@ int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u
     if (u_out) {
         l.uout = true;
         l.sp.u_out = u_out;
+    } else if (use_pair(c)) {
+        l.pair = true;
     } else if (use_bulk(c)) {
         if (c->num_sms <= 0) {
             int dev = 0, nsm = 0;
@@ -405,9 +416,11 @@ int64_t lbm_step_count(const lbm_ctx *c) { return c ? c->step : -1; }
 
 int lbm_set_kernel_variant(lbm_ctx *c, int variant)
 {
-    if (!c || variant < LBM_KERNEL_AUTO || variant > LBM_KERNEL_STAGED)
+    if (!c || variant < LBM_KERNEL_AUTO || variant > LBM_KERNEL_PAIRED)
         return LBM_ERR_ARG;
     if (variant == LBM_KERNEL_STAGED && !bulk_eligible(c))
+        return LBM_ERR_ARG;
+    if (variant == LBM_KERNEL_PAIRED && !pair_eligible(c))
         return LBM_ERR_ARG;
     c->kernel_variant = variant;
     return LBM_OK;
@@ -417,7 +430,7 @@ int lbm_kernel_variant_in_use(const lbm_ctx *c)
 {
     if (!c)
         return LBM_ERR_ARG;
-    return use_bulk(c) ? LBM_KERNEL_STAGED : LBM_KERNEL_PLAIN;
+    return use_pair(c) ? LBM_KERNEL_PAIRED : use_bulk(c) ? LBM_KERNEL_STAGED : LBM_KERNEL_PLAIN;
 }
 
 int lbm_macroscopic(lbm_ctx *c, void *p_out, void *u_out, int out_dtype)

@@ -142,12 +142,14 @@ __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coe
         rho = c.rho0;
         ir = c.inv_rho0;
     }
+    R jf[3];  // j + F/2 = rho u
     SFor<0, 3>::run([&](auto K_) {
         constexpr int k = decltype(K_)::value;
         if constexpr (FORCE)
-            u[k] = o_mul(o_fma(R(0.5), F[k], j[k]), ir);
+            jf[k] = o_fma(R(0.5), F[k], j[k]);
         else
-            u[k] = o_mul(j[k], ir);
+            jf[k] = j[k];
+        u[k] = o_mul(jf[k], ir);
     });
     const R uu = o_fma(u[2], u[2], o_fma(u[1], u[1], o_mul(u[0], u[0])));
     R A = o_fma(o_mul(R(-1.5), rho), uu, s);
@@ -161,35 +163,38 @@ __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coe
         constexpr int a = decltype(A_)::value;
         constexpr int b = opp<L>(a);
         const R t = R(L::w(a));
-        R eu = R(0), eF = R(0);
+        // e.u = (e.j') ir with j' = j (+ F/2): sums first, one product last
+        R ej = R(0), eF = R(0);
         (void)eF;
         SFor<0, 3>::run([&](auto K_) {
             constexpr int k = decltype(K_)::value;
             if constexpr (L::e(a, k) == 1) {
-                eu = o_add(eu, u[k]);
+                ej = o_add(ej, jf[k]);
                 if constexpr (FORCE)
                     eF = o_add(eF, F[k]);
             } else if constexpr (L::e(a, k) == -1) {
-                eu = o_sub(eu, u[k]);
+                ej = o_sub(ej, jf[k]);
                 if constexpr (FORCE)
                     eF = o_sub(eF, F[k]);
             }
         });
+        const R eu = o_mul(ej, ir);
         R sym = o_fma(o_mul(r45, eu), eu, A);
         R asym = o_mul(r3, eu);
         if constexpr (FORCE) {
             sym = o_fma(o_mul(o_mul(R(9), c.kf), eu), eF, sym);
             asym = o_fma(o_mul(R(3), c.kf), eF, asym);
         }
-        sym = o_mul(sym, t);
-        asym = o_mul(asym, t);
-        const R fa = o_add(sym, asym), fb = o_sub(sym, asym);
+        // no product feeds an add directly: each multiply-add is one
+        // explicit fma, so no compiler can fuse (and re-round) it differently
+        const R at = o_mul(asym, t);
+        const R fa = o_fma(sym, t, at), fb = o_fma(sym, t, -at);
         g[a] = o_fma(om, o_sub(fa, g[a]), g[a]);
         g[b] = o_fma(om, o_sub(fb, g[b]), g[b]);
     });
     {
         const R t0 = R(L::w(H));
-        g[H] = o_fma(om, o_sub(o_mul(t0, A), g[H]), g[H]);
+        g[H] = o_fma(om, o_fma(t0, A, -g[H]), g[H]);
     }
 }
 
@@ -651,6 +656,7 @@ struct Launch {
     AdjParams ap;
     size_t count;  // K_FLUSH
     bool bulk;     // K_STEP: use the shared-memory staged kernel (lbm_bulk.cuh)
+    bool pair;     // K_STEP: two nodes per thread, 32-bit accesses (lbm_pair.cuh)
     int bulk_nseg, bulk_xseg, num_sms;
     unsigned *err;  // error word for bounded waits
     dim3 grid, block;

@@ -5,6 +5,7 @@
 #include "lbm_adjoint.cuh"
 #include "lbm_bulk.cuh"
 #include "lbm_kernels.cuh"
+#include "lbm_pair.cuh"
 
 namespace lbm {
 
@@ -53,6 +54,27 @@ cudaError_t launch_storage(const Launch &l)
     using T = typename Sto<S>::T;
     const T *src = (const T *)l.src;
     T *dst = (T *)l.dst;
+    if (l.kind == K_STEP && l.pair) {
+        if constexpr (S == ST_F16S || S == ST_BF16S) {
+            const dim3 grid((l.sp.nx + 2 * kPairThreads - 1) / (2 * kPairThreads), l.sp.ny, l.sp.nz);
+            return with_bool(l.comp, [&](auto C) {
+                return with_bool(l.force, [&](auto Fo) {
+                    constexpr bool c = decltype(C)::value, fo = decltype(Fo)::value;
+                    const auto *s16 = (const unsigned short *)l.src;
+                    auto *d16 = (unsigned short *)l.dst;
+                    if (l.pattern == PAT_PULL)
+                        k_step_pair<L, S, PAT_PULL, c, fo><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                    else if (l.pattern == PAT_GATHER)
+                        k_step_pair<L, S, PAT_GATHER, c, fo><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                    else
+                        k_step_pair<L, S, PAT_LOCAL, c, fo><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                    return cudaGetLastError();
+                });
+            });
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     if (l.kind == K_STEP && l.bulk) {
         return with_bool(l.comp, [&](auto C) {
             return with_bool(l.force, [&](auto Fo) {

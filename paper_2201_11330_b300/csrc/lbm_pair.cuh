@@ -1,0 +1,430 @@
+// lbm_pair.cuh -- the fused step for 16-bit storage with two nodes per thread.
+//
+// Same arithmetic as k_step (lbm_kernels.cuh).  With 2-byte values, one value
+// per thread per slot makes every warp access 64 bytes, and HBM throughput
+// saturates well below the copy peak; here each thread owns the nodes x and
+// x+1 (x even) and moves one 32-bit word (two values) per slot.  Directions
+// with e_x = +-1 are realigned in registers: a thread loads the aligned word
+// holding its own positions and takes the missing half from its neighbour
+// lane with a warp shuffle (lanes at the warp edge load it, positions beyond
+// the row end take the wall or periodic value).  Pushed stores of the AA
+// pattern are realigned the same way, and a value is written with a 16-bit
+// store exactly where the aligned word would straddle two warps or the row
+// end, so no thread writes a location another thread owns.
+//
+// Ownership (AA pattern, in place): node x reads and writes only the slot
+// locations it owns, (x - e_a, abar) before and (x + e_a, a) after.  An
+// aligned 32-bit load may also fetch a half owned by a node of another warp;
+// that half is never used.  Inside a warp the shuffles order every lane's
+// loads before any lane's stores.
+//
+// Both nodes of a thread are collided together in packed FP32 arithmetic
+// (two lanes per instruction: __fadd2_rn, __fmul2_rn, __ffma2_rn), with
+// exactly the rounding sequence of the scalar collide(), so the results are
+// bitwise those of the one-node-per-thread kernel.
+//
+// Preconditions checked by the host: 16-bit storage, nx even.
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+// ---- packed FP32 (two nodes) -------------------------------------------------
+// Written as PTX with an explicit .rn rounding modifier, which forbids the
+// assembler from fusing a multiply into a following add: each operation
+// rounds exactly like its scalar __f*_rn counterpart in collide().
+__device__ __forceinline__ unsigned long long pk(float2 v)
+{
+    unsigned long long r;
+    memcpy(&r, &v, 8);
+    return r;
+}
+__device__ __forceinline__ float2 upk(unsigned long long r)
+{
+    float2 v;
+    memcpy(&v, &r, 8);
+    return v;
+}
+__device__ __forceinline__ float2 v_add(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 v_sub(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 v_mul(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 v_fma(float2 a, float2 b, float2 c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)), "l"(pk(c)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 v_bc(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 v_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// collide() of lbm_kernels.cuh on two nodes at once, operation for operation.
+template <class L, bool COMP, bool FORCE>
+__device__ __forceinline__ void collide2(float2 (&g)[L::Q], const float2 (&F)[3],
+                                         const Coef<float> &c)
+{
+    constexpr int H = L::Q / 2;
+    float2 sp[H], sm[H];
+    SFor<0, H>::run([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        sp[a] = v_add(g[a], g[opp<L>(a)]);
+        sm[a] = v_sub(g[a], g[opp<L>(a)]);
+    });
+    float2 s = g[H];
+    float2 j[3] = {v_bc(0.f), v_bc(0.f), v_bc(0.f)};
+    SFor<0, H>::run([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        s = v_add(s, sp[a]);
+        SFor<0, 3>::run([&](auto K_) {
+            constexpr int k = decltype(K_)::value;
+            if constexpr (L::e(a, k) == 1)
+                j[k] = v_add(j[k], sm[a]);
+            else if constexpr (L::e(a, k) == -1)
+                j[k] = v_sub(j[k], sm[a]);
+        });
+    });
+    float2 rho, ir;
+    if constexpr (COMP) {
+        rho = v_add(s, v_bc(c.sigma));
+        ir = make_float2(1.f / rho.x, 1.f / rho.y);
+    } else {
+        rho = v_bc(c.rho0);
+        ir = v_bc(c.inv_rho0);
+    }
+    float2 u[3], jf[3];
+    SFor<0, 3>::run([&](auto K_) {
+        constexpr int k = decltype(K_)::value;
+        if constexpr (FORCE)
+            jf[k] = v_fma(v_bc(0.5f), F[k], j[k]);
+        else
+            jf[k] = j[k];
+        u[k] = v_mul(jf[k], ir);
+    });
+    const float2 uu = v_fma(u[2], u[2], v_fma(u[1], u[1], v_mul(u[0], u[0])));
+    float2 A = v_fma(v_mul(v_bc(-1.5f), rho), uu, s);
+    if constexpr (FORCE) {
+        const float2 uF = v_fma(u[2], F[2], v_fma(u[1], F[1], v_mul(u[0], F[0])));
+        A = v_fma(v_bc(__fmul_rn(-3.f, c.kf)), uF, A);
+    }
+    const float2 r3 = v_mul(v_bc(3.f), rho), r45 = v_mul(v_bc(4.5f), rho);
+    const float2 om = v_bc(c.omega);
+    SFor<0, H>::run([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        constexpr int b = opp<L>(a);
+        const float2 t = v_bc(float(L::w(a)));
+        float2 ej = v_bc(0.f), eF = v_bc(0.f);
+        (void)eF;
+        SFor<0, 3>::run([&](auto K_) {
+            constexpr int k = decltype(K_)::value;
+            if constexpr (L::e(a, k) == 1) {
+                ej = v_add(ej, jf[k]);
+                if constexpr (FORCE)
+                    eF = v_add(eF, F[k]);
+            } else if constexpr (L::e(a, k) == -1) {
+                ej = v_sub(ej, jf[k]);
+                if constexpr (FORCE)
+                    eF = v_sub(eF, F[k]);
+            }
+        });
+        const float2 eu = v_mul(ej, ir);
+        float2 sym = v_fma(v_mul(r45, eu), eu, A);
+        float2 asym = v_mul(r3, eu);
+        if constexpr (FORCE) {
+            sym = v_fma(v_mul(v_bc(__fmul_rn(9.f, c.kf)), eu), eF, sym);
+            asym = v_fma(v_bc(__fmul_rn(3.f, c.kf)), eF, asym);
+        }
+        const float2 at = v_mul(asym, t);
+        const float2 fa = v_fma(sym, t, at), fb = v_fma(sym, t, v_neg(at));
+        g[a] = v_fma(om, v_sub(fa, g[a]), g[a]);
+        g[b] = v_fma(om, v_sub(fb, g[b]), g[b]);
+    });
+    {
+        const float2 t0 = v_bc(float(L::w(H)));
+        g[H] = v_fma(om, v_fma(t0, A, v_neg(g[H])), g[H]);
+    }
+}
+
+template <int S>
+__device__ __forceinline__ float2 dec2(unsigned w);
+template <>
+__device__ __forceinline__ float2 dec2<ST_F16S>(unsigned w)
+{
+    __half2 h;
+    memcpy(&h, &w, 4);
+    return __half22float2(h);
+}
+template <>
+__device__ __forceinline__ float2 dec2<ST_BF16S>(unsigned w)
+{
+    __nv_bfloat162 h;
+    memcpy(&h, &w, 4);
+    return __bfloat1622float2(h);
+}
+template <int S>
+__device__ __forceinline__ unsigned enc2(float2 v);
+template <>
+__device__ __forceinline__ unsigned enc2<ST_F16S>(float2 v)
+{
+    const __half2 h = __float22half2_rn(v);
+    unsigned w;
+    memcpy(&w, &h, 4);
+    return w;
+}
+template <>
+__device__ __forceinline__ unsigned enc2<ST_BF16S>(float2 v)
+{
+    const __nv_bfloat162 h = __float22bfloat162_rn(v);
+    unsigned w;
+    memcpy(&w, &h, 4);
+    return w;
+}
+
+constexpr int kPairThreads = 128;  // threads per block; 256 nodes per block
+
+__device__ __forceinline__ unsigned lo16(unsigned w) { return w & 0xffffu; }
+__device__ __forceinline__ unsigned hi16(unsigned w) { return w >> 16; }
+// (hi half of a, lo half of b) as (lo, hi) of the result
+__device__ __forceinline__ unsigned join_hi_lo(unsigned a, unsigned b)
+{
+    return __byte_perm(a, b, 0x5432);
+}
+
+// Source (pull) or target (push) row of direction a for row (y, z): the row
+// shifted by -e_a (pull) or +e_a (push) in y and z, wrapped on periodic axes;
+// `wall` when that row lies beyond a y or z wall.
+template <class L, int a, int SIGN, bool IROW = false>
+__device__ __forceinline__ int shifted_row(const StepParams &p, int y, int z, bool &wall)
+{
+    constexpr int ey = SIGN * L::e(a, 1), ez = SIGN * L::e(a, 2);
+    int ys = y + ey, zs = z + ez;
+    wall = false;
+    if constexpr (IROW)  // y and z have neighbours on both sides
+        return ys + p.ny * zs;
+    if (ys < 0 || ys >= p.ny) {
+        if (p.periodic & 2)
+            ys = ys < 0 ? ys + p.ny : ys - p.ny;
+        else
+            wall = true;
+    }
+    if (zs < 0 || zs >= p.nz) {
+        if (p.periodic & 4)
+            zs = zs < 0 ? zs + p.nz : zs - p.nz;
+        else
+            wall = true;
+    }
+    return ys + p.ny * zs;
+}
+
+template <class L, int S, int PAT, bool COMP, bool FORCE, bool IROW>
+__device__ __forceinline__ void pair_body(const unsigned short *src, unsigned short *dst,
+                                          const StepParams &p)
+{
+    using R = float;
+    constexpr int Q = L::Q;
+    const Coef<R> &c = p.cf;
+    const size_t N = (size_t)p.N;
+    const int nx = p.nx;
+    const int lane = threadIdx.x & 31;
+    const int x = 2 * (blockIdx.x * kPairThreads + threadIdx.x);
+    const int y = blockIdx.y, z = blockIdx.z;
+    const bool active = x < nx;
+    const int row = y + p.ny * z;
+    const size_t n = (size_t)row * nx + x;  // even
+    const bool xper = p.periodic & 1;
+    const bool top = p.lid_on && (y == p.ny - 1);
+
+    auto word = [&](const unsigned short *base, size_t i) -> unsigned {
+        return *reinterpret_cast<const unsigned *>(base + i);
+    };
+
+    // ---- gather the incoming pairs -------------------------------------------
+    // Phase 1 issues every load (aligned words, the warp-edge words, the
+    // wall/periodic values at the row ends) before any shuffle, so that all
+    // of them are in flight together; phase 2 realigns with shuffles.
+    unsigned W[Q], Wx[Q];  // Wx: the extra word (warp edge) or row-end value
+    SFor<0, Q>::run([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        constexpr int b = opp<L>(a);
+        constexpr int ex = L::e(a, 0);
+        Wx[a] = 0u;
+        if constexpr (PAT == PAT_LOCAL) {
+            W[a] = active ? word(src, (size_t)a * N + n) : 0u;
+            return;
+        }
+        // pull side: slot `ns` of the row shifted by -e_a, or the bounce
+        // slot `bs` of the node itself beyond a wall
+        constexpr int ns = (PAT == PAT_PULL) ? a : b;
+        constexpr int bs = (PAT == PAT_PULL) ? b : a;
+        bool yzw;
+        const int srow = shifted_row<L, a, -1, IROW>(p, y, z, yzw);
+        if (ex == 0 || yzw) {
+            W[a] = active ? word(src, (size_t)(yzw ? bs : ns) * N + (yzw ? n : (size_t)srow * nx + x))
+                          : 0u;
+            return;
+        }
+        const unsigned short *rbase = src + (size_t)ns * N + (size_t)srow * nx;
+        W[a] = active ? word(rbase, x) : 0u;
+        if constexpr (ex == 1) {
+            if (active && x == 0)  // position -1: periodic wrap or bounce-back
+                Wx[a] = xper ? rbase[nx - 1] : src[(size_t)bs * N + n];
+            else if (active && lane == 0)  // positions (x-2, x-1) lie in the previous warp's span
+                Wx[a] = word(rbase, x - 2);
+        } else {
+            if (active && x + 2 == nx)  // position nx: periodic wrap or bounce-back
+                Wx[a] = xper ? rbase[0] : src[(size_t)bs * N + n + 1];
+            else if (active && lane == 31)  // positions (x+2, x+3) lie in the next warp's span
+                Wx[a] = word(rbase, x + 2);
+        }
+    });
+    if constexpr (PAT != PAT_LOCAL) {
+        SFor<0, Q>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            constexpr int ex = L::e(a, 0);
+            if constexpr (ex != 0) {
+                bool yzw;
+                (void)shifted_row<L, a, -1, IROW>(p, y, z, yzw);
+                if (yzw)
+                    return;  // block-uniform
+                const unsigned w0 = W[a];
+                if constexpr (ex == 1) {
+                    // positions (x-1, x): hi of the previous word, lo of w0
+                    unsigned wp = __shfl_up_sync(0xffffffffu, w0, 1);
+                    if (lane == 0)
+                        wp = Wx[a];
+                    unsigned pr = join_hi_lo(wp, w0);
+                    if (x == 0)
+                        pr = (pr & 0xffff0000u) | Wx[a];
+                    W[a] = pr;
+                } else {
+                    // positions (x+1, x+2): hi of w0, lo of the next word
+                    unsigned wn = __shfl_down_sync(0xffffffffu, w0, 1);
+                    if (lane == 31)
+                        wn = Wx[a];
+                    unsigned pr = join_hi_lo(w0, wn);
+                    if (x + 2 == nx)
+                        pr = (pr & 0x0000ffffu) | (Wx[a] << 16);
+                    W[a] = pr;
+                }
+            }
+        });
+    }
+
+    // ---- collide nodes x and x+1 together (packed FP32) ------------------------
+    if (active) {
+        float2 g[Q];
+        SFor<0, Q>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            float2 v = dec2<S>(W[a]);
+            if constexpr (L::e(a, 1) == -1) {
+                if (top)
+                    v = make_float2(v.x + c.lid[a], v.y + c.lid[a]);
+            }
+            g[a] = v;
+        });
+        float2 F[3] = {v_bc(0.f), v_bc(0.f), v_bc(0.f)};
+        if constexpr (FORCE) {
+            for (int k = 0; k < L::D; ++k)
+                F[k] = *reinterpret_cast<const float2 *>(p.F + k * N + n);
+        }
+        collide2<L, COMP, FORCE>(g, F, c);
+        SFor<0, Q>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            W[a] = enc2<S>(g[a]);
+        });
+    }
+
+    // ---- store ---------------------------------------------------------------
+    auto put_word = [&](size_t i, unsigned w) { *reinterpret_cast<unsigned *>(dst + i) = w; };
+    SFor<0, Q>::run([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        constexpr int b = opp<L>(a);
+        constexpr int ex = L::e(a, 0);
+        const unsigned O = W[a];
+        if constexpr (PAT == PAT_PULL) {
+            if (active)
+                put_word((size_t)a * N + n, O);
+            return;
+        }
+        if constexpr (PAT == PAT_LOCAL) {
+            if (active)
+                put_word((size_t)b * N + n, O);
+            return;
+        }
+        // AA push of f*_a to x + e_a (slot a); beyond a wall: slot b of the node
+        bool yzw;
+        const int trow = shifted_row<L, a, +1, IROW>(p, y, z, yzw);
+        if (ex == 0 || yzw) {
+            if (active)
+                put_word(yzw ? (size_t)b * N + n : (size_t)a * N + (size_t)trow * nx + x, O);
+            return;
+        }
+        unsigned short *rbase = dst + (size_t)a * N + (size_t)trow * nx;
+        if constexpr (ex == 1) {
+            // targets (x+1, x+2); this lane writes the aligned word (x+2, x+3)
+            const unsigned On = __shfl_down_sync(0xffffffffu, O, 1);
+            if (!active)
+                return;
+            const bool last = lane == 31 || x + 2 >= nx;  // neighbour lane not in this row span
+            if (lane == 0)
+                rbase[x + 1] = (unsigned short)lo16(O);
+            if (x + 2 < nx) {
+                if (last)
+                    rbase[x + 2] = (unsigned short)hi16(O);
+                else
+                    put_word((size_t)a * N + (size_t)trow * nx + x + 2, join_hi_lo(O, On));
+            } else {  // node x+1 = nx-1 pushes beyond the row end
+                if (xper)
+                    rbase[0] = (unsigned short)hi16(O);
+                else
+                    dst[(size_t)b * N + n + 1] = (unsigned short)hi16(O);
+            }
+        } else {
+            // targets (x-1, x); this lane writes the aligned word (x-2, x-1)
+            const unsigned Op = __shfl_up_sync(0xffffffffu, O, 1);
+            if (!active)
+                return;
+            const bool last = lane == 31 || x + 2 >= nx;
+            if (x == 0) {  // node 0 pushes beyond the row start
+                if (xper)
+                    rbase[nx - 1] = (unsigned short)lo16(O);
+                else
+                    dst[(size_t)b * N + n] = (unsigned short)lo16(O);
+            } else if (lane == 0) {
+                rbase[x - 1] = (unsigned short)lo16(O);
+            } else {
+                put_word((size_t)a * N + (size_t)trow * nx + x - 2, join_hi_lo(Op, O));
+            }
+            if (last)
+                rbase[x] = (unsigned short)hi16(O);
+        }
+    });
+}
+
+template <class L, int S, int PAT, bool COMP, bool FORCE>
+__global__ void __launch_bounds__(kPairThreads) k_step_pair(const unsigned short *src,
+                                                            unsigned short *dst, const StepParams p)
+{
+    const int y = blockIdx.y, z = blockIdx.z;
+    const bool irow = y > 0 && y < p.ny - 1 && (L::D == 2 || (z > 0 && z < p.nz - 1));
+    if (irow || PAT == PAT_LOCAL)
+        pair_body<L, S, PAT, COMP, FORCE, true>(src, dst, p);
+    else
+        pair_body<L, S, PAT, COMP, FORCE, false>(src, dst, p);
+}
+
+}  // namespace lbm

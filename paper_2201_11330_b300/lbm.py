@@ -23,8 +23,9 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_STATE, LBM_ERR_NOME
 LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 = 0, 1, 2
 LBM_BC_PERIODIC, LBM_BC_CAVITY, LBM_BC_CHANNEL = 0, 1, 2
 LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = 0, 1, 2, 3
-LBM_KERNEL_AUTO, LBM_KERNEL_PLAIN, LBM_KERNEL_STAGED = 0, 1, 2
-KERNELS = {"auto": LBM_KERNEL_AUTO, "plain": LBM_KERNEL_PLAIN, "staged": LBM_KERNEL_STAGED}
+LBM_KERNEL_AUTO, LBM_KERNEL_PLAIN, LBM_KERNEL_STAGED, LBM_KERNEL_PAIRED = 0, 1, 2, 3
+KERNELS = {"auto": LBM_KERNEL_AUTO, "plain": LBM_KERNEL_PLAIN, "staged": LBM_KERNEL_STAGED,
+           "paired": LBM_KERNEL_PAIRED}
 
 LATTICES = {"d2q9": LBM_D2Q9, "d3q19": LBM_D3Q19, "d3q27": LBM_D3Q27}
 BCS = {"periodic": LBM_BC_PERIODIC, "cavity": LBM_BC_CAVITY, "channel": LBM_BC_CHANNEL}
@@ -35,7 +36,8 @@ QD = {LBM_D2Q9: (9, 2), LBM_D3Q19: (19, 3), LBM_D3Q27: (27, 3)}
 EXPORTS = [
     "lbm_default_opts", "lbm_tau_from_paper", "lbm_workspace_bytes", "lbm_create",
     "lbm_set_stream", "lbm_init", "lbm_set_force", "lbm_set_lid", "lbm_step",
-    "lbm_step_count", "lbm_set_kernel_variant", "lbm_kernel_variant_in_use", "lbm_macroscopic", "lbm_reduce", "lbm_state_bytes", "lbm_get_state",
+    "lbm_step_count", "lbm_set_kernel_variant", "lbm_kernel_variant_in_use",
+    "lbm_macroscopic", "lbm_reduce", "lbm_state_bytes", "lbm_get_state",
     "lbm_set_state", "lbm_adjoint_workspace_bytes", "lbm_adjoint_forward",
     "lbm_adjoint_backward", "lbm_adjoint", "lbm_reduce_state_noalloc", "lbm_error_string",
     "lbm_destroy",
@@ -338,14 +340,15 @@ class Lattice:
         return lbm_step_count(self.ctx)
 
     def set_kernel(self, variant):
-        """'auto', 'plain' or 'staged' (see lbm_set_kernel_variant)."""
+        """'auto', 'plain', 'staged' or 'paired' (see lbm_set_kernel_variant)."""
         lbm_set_kernel_variant(self.ctx, _key(KERNELS, variant))
         return self
 
     @property
     def kernel(self):
         v = lbm_kernel_variant_in_use(self.ctx)
-        return {LBM_KERNEL_PLAIN: "plain", LBM_KERNEL_STAGED: "staged"}[v]
+        return {LBM_KERNEL_PLAIN: "plain", LBM_KERNEL_STAGED: "staged",
+                LBM_KERNEL_PAIRED: "paired"}[v]
 
     def macroscopic(self, dtype=None):
         """(p (N,), u (d, N)) of the current step."""

@@ -351,3 +351,24 @@ def test_staged_parity_with_oracle(lattice, shape, bc, storage):
         eu, ep = errors((p.cpu().numpy(), u.cpu().numpy()), ref, 0.05)
         assert eu < TOL[storage] and ep < 10 * TOL[storage], (aa, eu, ep)
         assert lat.reduce()["mass"] > 0  # also checks the staged kernel's error word
+
+
+# ---------------------------------------------------------------------------
+# The paired kernel (16-bit storage, two nodes per thread, shuffle realignment)
+# against the plain kernel: bitwise equal, including row ends, warp and block
+# edges, ragged blocks and 2-node rows.
+
+PAIRED_SHAPES = [("d3q19", (520, 9, 7)), ("d3q19", (66, 13, 11)), ("d3q27", (264, 7, 6)),
+                 ("d2q9", (300, 37, 1)), ("d3q19", (2, 3, 3)), ("d3q27", (4, 1, 5)),
+                 ("d2q9", (2, 5, 1)), ("d3q19", (258, 5, 4))]
+
+
+@pytest.mark.parametrize("lattice,shape", PAIRED_SHAPES)
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+@pytest.mark.parametrize("bc", ["cavity", "periodic", "channel"])
+def test_paired_equals_plain_bitwise(lattice, shape, storage, bc):
+    for aa, steps, force in ((False, 9, True), (True, 9, False), (True, 10, True),
+                             (True, 7, True)):
+        a = _staged_run(lattice, shape, bc, storage, aa, steps, "plain", force)
+        b = _staged_run(lattice, shape, bc, storage, aa, steps, "paired", force)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), (aa, steps, force)
