@@ -228,8 +228,9 @@ def run_cavity(lattice, n, re, storage, aa, steps, warmup, world, device):
 
 def run_e2e(n, re, storage, steps, warmup, world, device):
     """Public API with host buffers: pinned-host initial fields -> device,
-    lbm_init, then per step lbm_step + lbm_reduce (Monitor; 48 B to host),
-    final macroscopic fields -> pinned host.  All inside the timed region."""
+    lbm_init, then per step lbm_step_reduce (the step with the Monitor fused
+    in; 48 B to host), final macroscopic fields -> pinned host.  All inside
+    the timed region."""
     import torch
     from paper_2201_11330_b300 import workloads as W
     from paper_2201_11330_b300.lbm import Lattice
@@ -250,8 +251,7 @@ def run_e2e(n, re, storage, steps, warmup, world, device):
         u_dev.copy_(u_host, non_blocking=True)
         lat.init(p_dev, u_dev)
         for _ in range(nsteps):
-            lat.step(1)
-            lat.reduce()
+            lat.step_reduce(1)
         lat.macroscopic_into(p_o, u_o)
         p_out.copy_(p_o, non_blocking=True)
         u_out.copy_(u_o, non_blocking=True)
@@ -270,8 +270,9 @@ def run_e2e(n, re, storage, steps, warmup, world, device):
            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": 48 + d2h / steps,
            "steps": steps,
            "what": f"D3Q19 cavity {n}^3 {storage} AA via paper_2201_11330_b300.lbm.Lattice: "
-                   "pinned-host FP64 initial (p, u) -> device, lbm_init, per step lbm_step(1) + "
-                   "lbm_reduce (FP64 monitor to host), final FP32 (p, u) -> pinned host"}
+                   "pinned-host FP64 initial (p, u) -> device, lbm_init, per step "
+                   "lbm_step_reduce(1) (step with the FP64 monitor fused in, 48 B to host), "
+                   "final FP32 (p, u) -> pinned host"}
     del lat
     torch.cuda.empty_cache()
     return res

@@ -158,6 +158,14 @@ int lbm_set_kernel_variant(lbm_ctx *ctx, int variant);
 /* The variant lbm_step currently launches (PLAIN, STAGED or PAIRED). */
 int lbm_kernel_variant_in_use(const lbm_ctx *ctx);
 
+/* lbm_step(n) whose last step also computes the Monitor values of
+ * lbm_reduce (same definitions, out: host, 6 doubles) inside the step
+ * kernel: per-block sums written by the step itself, then a fixed-order
+ * FP64 reduction of those (deterministic).  Saves the separate read of the
+ * whole state that lbm_reduce needs.  n >= 1.  Synchronises the stream.
+ * Errors as lbm_step and lbm_reduce. */
+int lbm_step_reduce(lbm_ctx *ctx, int64_t n, double *out);
+
 /* Sec. 3.4 PostProcessing: p = c_s^2 sum f and u = (sum e f + F/2)/rho of
  * the current step.  p_out: device, N values, or NULL; u_out: device, d*N
  * values component-major, or NULL.  out_dtype: 0 = FP64, 1 = FP32. */

@@ -241,8 +241,8 @@ __device__ __forceinline__ void bulk_node(const typename Sto<S>::T *src, typenam
             F[k] = R(p.F[k * N + n]);
         });
     }
-    R u[3];
-    collide<L, R, COMP, FORCE>(g, F, c, u);
+    R u[3], s_, rho_;
+    collide<L, R, COMP, FORCE>(g, F, c, u, s_, rho_);
     if constexpr (PAT == PAT_PULL) {
         SFor<0, Q>::run([&](auto A_) {
             constexpr int a = decltype(A_)::value;

@@ -10,6 +10,7 @@
 #include "lbm.h"
 #include "lbm_bulk.cuh"
 #include "lbm_capi_internal.h"
+#include "lbm_pair.cuh"
 #include "lbm_kernels.cuh"
 
 using namespace lbm;
@@ -56,8 +57,9 @@ bool valid_opts(const lbm_opts &o)
 }
 
 struct Layout {
-    size_t state_bytes, f_off[2], partial_off, result_off, total;
+    size_t state_bytes, f_off[2], partial_off, result_off, step_partial_off, total;
     int nred;
+    long long step_blocks;
 };
 
 Layout layout_for(int lattice, int nx, int ny, int nz, const lbm_opts &o)
@@ -78,6 +80,11 @@ Layout layout_for(int lattice, int nx, int ny, int nz, const lbm_opts &o)
     off += align_up((size_t)L.nred * kPartialStride * sizeof(double));
     L.result_off = off;
     off += kAlign;
+    // one monitor partial per block of a step launch (the plain kernel has the
+    // most blocks of all step kernels)
+    L.step_blocks = nseg;
+    L.step_partial_off = off;
+    off += align_up((size_t)L.step_blocks * kPartialStride * sizeof(double));
     L.total = off;
     return L;
 }
@@ -160,12 +167,18 @@ bool use_bulk(const lbm_ctx *c)
     return c->kernel_variant == LBM_KERNEL_STAGED && bulk_eligible(c);
 }
 
-bool use_pair(const lbm_ctx *c)
+bool use_pair(const lbm_ctx *c, int pattern = PAT_PULL)
 {
     if (!pair_eligible(c))
         return false;
-    // automatic choice (measured): paired for 16-bit storage
-    return c->kernel_variant == LBM_KERNEL_PAIRED || c->kernel_variant == LBM_KERNEL_AUTO;
+    if (c->kernel_variant == LBM_KERNEL_PAIRED)
+        return true;
+    if (c->kernel_variant != LBM_KERNEL_AUTO)
+        return false;
+    // automatic choice (measured on B300): paired for 16-bit storage, except
+    // the D3Q27 AA gather half, where its 18 shifted directions cost more
+    // than the plain kernel
+    return !(c->lattice == LBM_D3Q27 && pattern == PAT_GATHER);
 }
 
 Launch base_launch(const lbm_ctx *c, int kind)
@@ -193,18 +206,24 @@ Launch ctx_base_launch(const lbm_ctx *c, int kind) { return base_launch(c, kind)
 
 cudaError_t ctx_dispatch(const lbm_ctx *c, const Launch &l) { return dispatch(c->lattice, l); }
 
-int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u_out)
+int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u_out,
+                    long long *reduce_blocks)
 {
     Launch l = base_launch(c, K_STEP);
     l.pattern = pattern;
     l.src = src;
     l.dst = dst;
+    if (reduce_blocks)
+        l.sp.partials = c->step_partials;
     if (u_out) {
         l.uout = true;
         l.sp.u_out = u_out;
-    } else if (use_pair(c)) {
+    } else if (use_pair(c, pattern)) {
         l.pair = true;
-    } else if (use_bulk(c)) {
+        if (reduce_blocks)
+            *reduce_blocks = (long long)((c->nx + 2 * kPairThreads - 1) / (2 * kPairThreads)) *
+                             c->ny * c->nz;
+    } else if (use_bulk(c) && !reduce_blocks) {
         if (c->num_sms <= 0) {
             int dev = 0, nsm = 0;
             if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -218,6 +237,8 @@ int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u
         l.num_sms = c->num_sms;
         l.err = c->err;
     }
+    if (reduce_blocks && !l.pair)
+        *reduce_blocks = (long long)l.grid.x * l.grid.y * l.grid.z;
     return dispatch(c->lattice, l) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
@@ -323,6 +344,8 @@ int lbm_create(int lattice, int nx, int ny, int nz, double tau, int bc, const lb
     c->nred = L.nred;
     c->partials = (double *)(c->ws + L.partial_off);
     c->result = (double *)(c->ws + L.result_off);
+    c->step_partials = (double *)(c->ws + L.step_partial_off);
+    c->step_blocks = L.step_blocks;
     c->stream = (cudaStream_t)cuda_stream;
     c->force = nullptr;
     c->step = 0;
@@ -433,6 +456,51 @@ int lbm_kernel_variant_in_use(const lbm_ctx *c)
     return use_pair(c) ? LBM_KERNEL_PAIRED : use_bulk(c) ? LBM_KERNEL_STAGED : LBM_KERNEL_PLAIN;
 }
 
+int lbm_step_reduce(lbm_ctx *c, int64_t n, double *out)
+{
+    if (!c || n < 1 || !out)
+        return LBM_ERR_ARG;
+    if (!c->initialized)
+        return LBM_ERR_STATE;
+    int rc = lbm_step(c, n - 1);
+    if (rc != LBM_OK)
+        return rc;
+    long long nb = 0;
+    if (c->opts.aa) {
+        const int pat = (c->step % 2 == 0) ? PAT_GATHER : PAT_LOCAL;
+        rc = ctx_launch_step(c, c->f[0], c->f[0], pat, nullptr, &nb);
+    } else {
+        rc = ctx_launch_step(c, c->f[c->cur], c->f[1 - c->cur], PAT_PULL, nullptr, &nb);
+        if (rc == LBM_OK)
+            c->cur = 1 - c->cur;
+    }
+    if (rc != LBM_OK)
+        return rc;
+    ++c->step;
+    const int nout = (int)(nb < c->nred ? nb : c->nred);
+    if (launch_chunks(c->step_partials, nb, c->partials, nout, c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    if (launch_finish(c->partials, nout, c->result, c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    double r[12];
+    if (cudaMemcpyAsync(r, c->result, sizeof(r), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    unsigned errword;
+    memcpy(&errword, (const char *)r + 64, sizeof(errword));
+    if (errword != 0)
+        return LBM_ERR_CUDA;
+    out[0] = r[0] + (c->shifted ? (double)c->N : 0.0);
+    for (int k = 1; k < 5; ++k)
+        out[k] = r[k];
+    out[5] = sqrt(r[5]);
+    for (int k = 0; k < kReduceVals; ++k)
+        if (!isfinite(out[k]))
+            return LBM_ERR_UNSTABLE;
+    return LBM_OK;
+}
+
 int lbm_macroscopic(lbm_ctx *c, void *p_out, void *u_out, int out_dtype)
 {
     if (!c || (out_dtype != 0 && out_dtype != 1))
@@ -534,6 +602,13 @@ namespace lbm {
 cudaError_t launch_finish(const double *partials, int nblocks, double *out, cudaStream_t s)
 {
     k_reduce_finish<<<1, 256, 0, s>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chunks(const double *in, long long nin, double *out, int nout, cudaStream_t s)
+{
+    const long long chunk = (nin + nout - 1) / nout;
+    k_reduce_chunks<<<nout, 256, 0, s>>>(in, nin, chunk, out);
     return cudaGetLastError();
 }
 }  // namespace lbm

@@ -24,6 +24,8 @@ struct lbm_ctx {
     int nred;  // moment-kernel blocks (reduction partials)
     double *partials;
     double *result;
+    double *step_partials;  // per-block monitor sums of a reducing step
+    long long step_blocks;  // capacity of step_partials (blocks)
     cudaStream_t stream;
     const float *force;
     int64_t step;
@@ -43,7 +45,8 @@ struct lbm_ctx {
 namespace lbm {
 lbm::Launch ctx_base_launch(const lbm_ctx *c, int kind);
 cudaError_t ctx_dispatch(const lbm_ctx *c, const lbm::Launch &l);
-int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u_out);
+int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u_out,
+                    long long *reduce_blocks = nullptr);
 int ctx_launch_moments(lbm_ctx *c, const void *src, int form, void *p_out, void *u_out,
                        int out_f32, double *partials);
 int ctx_current_form(const lbm_ctx *c);

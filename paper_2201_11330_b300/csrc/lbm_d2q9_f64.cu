@@ -1,0 +1,6 @@
+// lbm_d2q9_f64.cu -- kernel instantiations for D2Q9 with F64 storage.
+#include "lbm_launch.cuh"
+
+namespace lbm {
+cudaError_t launch_d2q9_f64(const Launch &l) { return launch_storage<D2Q9, ST_F64>(l); }
+}  // namespace lbm

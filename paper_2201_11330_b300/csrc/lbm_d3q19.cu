@@ -1,6 +1,25 @@
-// lbm_d3q19.cu -- instantiation unit for the D3Q19 velocity set (Sec. 2.1).
-#include "lbm_launch.cuh"
+// lbm_d3q19.cu -- storage dispatch for the D3Q19 velocity set (Sec. 2.1); the
+// kernels of each storage type are instantiated in lbm_d3q19_<storage>.cu.
+#include "lbm_kernels.cuh"
 
 namespace lbm {
-cudaError_t launch_d3q19(const Launch &l) { return launch_lattice<D3Q19>(l); }
+cudaError_t launch_d3q19_f64(const Launch &l);
+cudaError_t launch_d3q19_f32(const Launch &l);
+cudaError_t launch_d3q19_f16s(const Launch &l);
+cudaError_t launch_d3q19_bf16s(const Launch &l);
+
+cudaError_t launch_d3q19(const Launch &l)
+{
+    switch (l.storage) {
+    case ST_F64:
+        return launch_d3q19_f64(l);
+    case ST_F32:
+        return launch_d3q19_f32(l);
+    case ST_F16S:
+        return launch_d3q19_f16s(l);
+    case ST_BF16S:
+        return launch_d3q19_bf16s(l);
+    }
+    return cudaErrorInvalidValue;
+}
 }  // namespace lbm

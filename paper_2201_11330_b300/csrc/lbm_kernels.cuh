@@ -51,6 +51,7 @@ struct StepParams {
     int lid_on;    // the +y wall moves
     Coef<float> cf;
     Coef<double> cd;
+    double *partials;  // per-block monitor sums (RED kernels)
     const float *F;  // body force, d*N component-major (FORCE kernels)
     void *u_out;     // velocity output, d*N component-major, kernel arithmetic type (UOUT)
 };
@@ -112,7 +113,7 @@ __device__ __forceinline__ double o_fma(double a, double b, double c) { return _
 //   A = sum g - 1.5 rho u.u  (the sigma*t_a shift cancels).
 template <class L, class R, bool COMP, bool FORCE>
 __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coef<R> &c,
-                                        R (&u)[3])
+                                        R (&u)[3], R &s_out, R &rho_out)
 {
     constexpr int H = L::Q / 2;
     R sp[H], sm[H];
@@ -142,6 +143,8 @@ __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coe
         rho = c.rho0;
         ir = c.inv_rho0;
     }
+    s_out = s;
+    rho_out = rho;
     R jf[3];  // j + F/2 = rho u
     SFor<0, 3>::run([&](auto K_) {
         constexpr int k = decltype(K_)::value;
@@ -285,12 +288,60 @@ __device__ __forceinline__ void make_axes(const StepParams &p, int x, int y, int
     }
 }
 
+// ---- monitor values of one node (Sec. 3.4 Monitor) ---------------------------
+// sum P (shifted: sum g), momentum rho u, kinetic energy rho |u|^2 / 2, |u|^2.
+template <class R>
+__device__ __forceinline__ void monitor_values(R s, R rho, const R (&u)[3], R (&mon)[6])
+{
+    const R uu = o_fma(u[2], u[2], o_fma(u[1], u[1], o_mul(u[0], u[0])));
+    mon[0] = s;
+    mon[1] = o_mul(rho, u[0]);
+    mon[2] = o_mul(rho, u[1]);
+    mon[3] = o_mul(rho, u[2]);
+    mon[4] = o_mul(o_mul(R(0.5), rho), uu);
+    mon[5] = uu;
+}
+
+template <class R>
+__device__ __forceinline__ R warp_sum(R v);
+template <class R>
+__device__ __forceinline__ R warp_max(R v);
+
+// Block-wide monitor sums of the launch's nodes (warp in the kernel's
+// arithmetic, across warps in FP64, fixed order), written to
+// partials[block * 8 + k].  Every thread of the block must call it.
+template <class R>
+__device__ __forceinline__ void block_monitor(const R (&mon)[6], double *partials)
+{
+    __shared__ double sh[32][6];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    R w[6];
+    for (int k = 0; k < 5; ++k)
+        w[k] = warp_sum(mon[k]);
+    w[5] = warp_max(mon[5]);
+    if (lane == 0)
+        for (int k = 0; k < 6; ++k)
+            sh[warp][k] = double(w[k]);
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        double r = sh[0][k];
+        for (int i = 1; i < nwarps; ++i)
+            r = (k == 5) ? fmax(r, sh[i][k]) : r + sh[i][k];
+        const size_t b = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+        partials[b * kPartialStride + k] = r;
+    }
+}
+
 // ---- one node of one time step ----------------------------------------------
 // INTERIOR: the node's row has neighbours inside the box in y and z (no wall,
 // no wrap), so only the x axis needs per-thread boundary logic.
-template <class L, int S, int PAT, bool COMP, bool FORCE, bool UOUT, bool INTERIOR>
+template <class L, int S, int PAT, bool COMP, bool FORCE, bool UOUT, bool INTERIOR,
+          bool RED = false>
 __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typename Sto<S>::T *dst,
-                                          const StepParams &p, int x, int y, int z)
+                                          const StepParams &p, int x, int y, int z,
+                                          typename Sto<S>::R (&mon)[6])
 {
     using T = typename Sto<S>::T;
     using R = typename Sto<S>::R;
@@ -345,8 +396,10 @@ __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typenam
             F[k] = R(p.F[k * N + n]);
         });
     }
-    R u[3];
-    collide<L, R, COMP, FORCE>(g, F, c, u);
+    R u[3], s_, rho_;
+    collide<L, R, COMP, FORCE>(g, F, c, u, s_, rho_);
+    if constexpr (RED)
+        monitor_values(s_, rho_, u, mon);
     if constexpr (UOUT) {
         SFor<0, L::D>::run([&](auto K_) {
             constexpr int k = decltype(K_)::value;
@@ -377,27 +430,35 @@ __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typenam
 }
 
 // grid: (ceil(nx/blockDim.x), ny, nz); one node per thread.
-template <class L, int S, int PAT, bool COMP, bool FORCE, bool UOUT>
+template <class L, int S, int PAT, bool COMP, bool FORCE, bool UOUT, bool RED = false>
 // (__launch_bounds__ with an explicit minimum of 1 block lets nvcc roughly
 // double the register count of these kernels and halves their occupancy;
 // the thread bound alone keeps them at 40-48 registers.)
 __global__ void __launch_bounds__(256) k_step(const typename Sto<S>::T *src,
                                               typename Sto<S>::T *dst, const StepParams p)
 {
+    using R = typename Sto<S>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= p.nx)
-        return;
-    if constexpr (PAT == PAT_LOCAL) {
-        step_node<L, S, PAT, COMP, FORCE, UOUT, true>(src, dst, p, x, y, z);
-    } else {
-        const bool interior =
-            y > 0 && y < p.ny - 1 && (L::D == 2 || (z > 0 && z < p.nz - 1));
-        if (interior)
-            step_node<L, S, PAT, COMP, FORCE, UOUT, true>(src, dst, p, x, y, z);
-        else
-            step_node<L, S, PAT, COMP, FORCE, UOUT, false>(src, dst, p, x, y, z);
+    if constexpr (!RED) {  // no block-wide step follows: idle threads may leave
+        if (x >= p.nx)
+            return;
     }
+    R mon[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    if (x < p.nx) {
+        if constexpr (PAT == PAT_LOCAL) {
+            step_node<L, S, PAT, COMP, FORCE, UOUT, true, RED>(src, dst, p, x, y, z, mon);
+        } else {
+            const bool interior =
+                y > 0 && y < p.ny - 1 && (L::D == 2 || (z > 0 && z < p.nz - 1));
+            if (interior)
+                step_node<L, S, PAT, COMP, FORCE, UOUT, true, RED>(src, dst, p, x, y, z, mon);
+            else
+                step_node<L, S, PAT, COMP, FORCE, UOUT, false, RED>(src, dst, p, x, y, z, mon);
+        }
+    }
+    if constexpr (RED)
+        block_monitor(mon, p.partials);
 }
 
 // ---- initialisation (Sec. 2.2: f = feq(p, u), then the first collision) -----
@@ -442,8 +503,8 @@ __global__ void __launch_bounds__(256) k_init(typename Sto<S>::T *dst, const Ste
         R F[3] = {R(0), R(0), R(0)};
         for (int k = 0; k < L::D; ++k)
             F[k] = R(p.F[k * N + n]);
-        R uc[3];
-        collide<L, R, COMP, true>(g, F, c, uc);
+        R uc[3], s_, rho_;
+        collide<L, R, COMP, true>(g, F, c, uc, s_, rho_);
     }
     SFor<0, Q>::run([&](auto A_) {
         constexpr int a = decltype(A_)::value;
@@ -628,6 +689,33 @@ static __global__ void __launch_bounds__(256) k_reduce_finish(const double *part
         out[threadIdx.x] = sh[0][threadIdx.x];
 }
 
+// First stage of the fused monitor: block b sums partials [b*chunk, (b+1)*chunk)
+// of the step kernel's blocks, in order, into out[b].
+static __global__ void __launch_bounds__(256) k_reduce_chunks(const double *in, long long nin,
+                                                              long long chunk, double *out)
+{
+    __shared__ double sh[256][kReduceVals];
+    double acc[kReduceVals] = {0, 0, 0, 0, 0, 0};
+    const long long lo = blockIdx.x * chunk;
+    const long long hi = lo + chunk < nin ? lo + chunk : nin;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        for (int k = 0; k < kReduceVals; ++k)
+            acc[k] = (k == 5) ? fmax(acc[k], in[i * kPartialStride + k])
+                              : acc[k] + in[i * kPartialStride + k];
+    for (int k = 0; k < kReduceVals; ++k)
+        sh[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < kReduceVals; ++k)
+                sh[threadIdx.x][k] = (k == 5) ? fmax(sh[threadIdx.x][k], sh[threadIdx.x + s][k])
+                                              : sh[threadIdx.x][k] + sh[threadIdx.x + s][k];
+        __syncthreads();
+    }
+    if (threadIdx.x < kReduceVals)
+        out[blockIdx.x * kPartialStride + threadIdx.x] = sh[0][threadIdx.x];
+}
+
 // ---- adjoint parameters (kernels in lbm_adjoint.cuh) -------------------------
 struct AdjParams {
     const void *lam_in;   // lambda^{k+1}, Q*N (R)
@@ -668,5 +756,6 @@ cudaError_t launch_d2q9(const Launch &l);
 cudaError_t launch_d3q19(const Launch &l);
 cudaError_t launch_d3q27(const Launch &l);
 cudaError_t launch_finish(const double *partials, int nblocks, double *out, cudaStream_t s);
+cudaError_t launch_chunks(const double *in, long long nin, double *out, int nout, cudaStream_t s);
 
 }  // namespace lbm

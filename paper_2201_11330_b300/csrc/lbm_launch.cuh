@@ -62,13 +62,16 @@ cudaError_t launch_storage(const Launch &l)
                     constexpr bool c = decltype(C)::value, fo = decltype(Fo)::value;
                     const auto *s16 = (const unsigned short *)l.src;
                     auto *d16 = (unsigned short *)l.dst;
-                    if (l.pattern == PAT_PULL)
-                        k_step_pair<L, S, PAT_PULL, c, fo><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
-                    else if (l.pattern == PAT_GATHER)
-                        k_step_pair<L, S, PAT_GATHER, c, fo><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
-                    else
-                        k_step_pair<L, S, PAT_LOCAL, c, fo><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
-                    return cudaGetLastError();
+                    return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
+                        constexpr bool rd = decltype(Rd)::value;
+                        if (l.pattern == PAT_PULL)
+                            k_step_pair<L, S, PAT_PULL, c, fo, rd><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                        else if (l.pattern == PAT_GATHER)
+                            k_step_pair<L, S, PAT_GATHER, c, fo, rd><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                        else
+                            k_step_pair<L, S, PAT_LOCAL, c, fo, rd><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                        return cudaGetLastError();
+                    });
                 });
             });
         } else {
@@ -99,26 +102,32 @@ cudaError_t launch_storage(const Launch &l)
             }
             return with_bool(l.comp, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
-                    k_step<L, S, PAT_PULL, decltype(C)::value, decltype(Fo)::value, false>
-                        <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
-                    return cudaGetLastError();
+                    return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
+                        k_step<L, S, PAT_PULL, decltype(C)::value, decltype(Fo)::value, false,
+                               decltype(Rd)::value><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                        return cudaGetLastError();
+                    });
                 });
             });
         }
         if (l.pattern == PAT_GATHER) {
             return with_bool(l.comp, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
-                    k_step<L, S, PAT_GATHER, decltype(C)::value, decltype(Fo)::value, false>
-                        <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
-                    return cudaGetLastError();
+                    return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
+                        k_step<L, S, PAT_GATHER, decltype(C)::value, decltype(Fo)::value, false,
+                               decltype(Rd)::value><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                        return cudaGetLastError();
+                    });
                 });
             });
         }
         return with_bool(l.comp, [&](auto C) {
             return with_bool(l.force, [&](auto Fo) {
-                k_step<L, S, PAT_LOCAL, decltype(C)::value, decltype(Fo)::value, false>
-                    <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
-                return cudaGetLastError();
+                return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
+                    k_step<L, S, PAT_LOCAL, decltype(C)::value, decltype(Fo)::value, false,
+                           decltype(Rd)::value><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                    return cudaGetLastError();
+                });
             });
         });
     }
@@ -173,20 +182,6 @@ cudaError_t launch_storage(const Launch &l)
     return cudaErrorInvalidValue;
 }
 
-template <class L>
-cudaError_t launch_lattice(const Launch &l)
-{
-    switch (l.storage) {
-    case ST_F64:
-        return launch_storage<L, ST_F64>(l);
-    case ST_F32:
-        return launch_storage<L, ST_F32>(l);
-    case ST_F16S:
-        return launch_storage<L, ST_F16S>(l);
-    case ST_BF16S:
-        return launch_storage<L, ST_BF16S>(l);
-    }
-    return cudaErrorInvalidValue;
-}
+
 
 }  // namespace lbm

@@ -76,7 +76,8 @@ __device__ __forceinline__ float2 v_neg(float2 a) { return make_float2(-a.x, -a.
 // collide() of lbm_kernels.cuh on two nodes at once, operation for operation.
 template <class L, bool COMP, bool FORCE>
 __device__ __forceinline__ void collide2(float2 (&g)[L::Q], const float2 (&F)[3],
-                                         const Coef<float> &c)
+                                         const Coef<float> &c, float2 (&u_out)[3], float2 &s_out,
+                                         float2 &rho_out)
 {
     constexpr int H = L::Q / 2;
     float2 sp[H], sm[H];
@@ -106,6 +107,8 @@ __device__ __forceinline__ void collide2(float2 (&g)[L::Q], const float2 (&F)[3]
         rho = v_bc(c.rho0);
         ir = v_bc(c.inv_rho0);
     }
+    s_out = s;
+    rho_out = rho;
     float2 u[3], jf[3];
     SFor<0, 3>::run([&](auto K_) {
         constexpr int k = decltype(K_)::value;
@@ -157,6 +160,9 @@ __device__ __forceinline__ void collide2(float2 (&g)[L::Q], const float2 (&F)[3]
         const float2 t0 = v_bc(float(L::w(H)));
         g[H] = v_fma(om, v_fma(t0, A, v_neg(g[H])), g[H]);
     }
+    u_out[0] = u[0];
+    u_out[1] = u[1];
+    u_out[2] = u[2];
 }
 
 template <int S>
@@ -230,7 +236,7 @@ __device__ __forceinline__ int shifted_row(const StepParams &p, int y, int z, bo
     return ys + p.ny * zs;
 }
 
-template <class L, int S, int PAT, bool COMP, bool FORCE, bool IROW>
+template <class L, int S, int PAT, bool COMP, bool FORCE, bool IROW, bool RED>
 __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned short *dst,
                                           const StepParams &p)
 {
@@ -324,6 +330,7 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
         });
     }
 
+    float mon[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     // ---- collide nodes x and x+1 together (packed FP32) ------------------------
     if (active) {
         float2 g[Q];
@@ -341,11 +348,21 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
             for (int k = 0; k < L::D; ++k)
                 F[k] = *reinterpret_cast<const float2 *>(p.F + k * N + n);
         }
-        collide2<L, COMP, FORCE>(g, F, c);
+        float2 u2[3], s2, rho2;
+        collide2<L, COMP, FORCE>(g, F, c, u2, s2, rho2);
         SFor<0, Q>::run([&](auto A_) {
             constexpr int a = decltype(A_)::value;
             W[a] = enc2<S>(g[a]);
         });
+        if constexpr (RED) {  // the two nodes' monitor values, summed in the thread
+            float m0[6], m1[6];
+            const float ua[3] = {u2[0].x, u2[1].x, u2[2].x}, ub[3] = {u2[0].y, u2[1].y, u2[2].y};
+            monitor_values(s2.x, rho2.x, ua, m0);
+            monitor_values(s2.y, rho2.y, ub, m1);
+            for (int k = 0; k < 5; ++k)
+                mon[k] = o_add(m0[k], m1[k]);
+            mon[5] = fmaxf(m0[5], m1[5]);
+        }
     }
 
     // ---- store ---------------------------------------------------------------
@@ -413,18 +430,20 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
                 rbase[x] = (unsigned short)hi16(O);
         }
     });
+    if constexpr (RED)
+        block_monitor(mon, p.partials);
 }
 
-template <class L, int S, int PAT, bool COMP, bool FORCE>
+template <class L, int S, int PAT, bool COMP, bool FORCE, bool RED = false>
 __global__ void __launch_bounds__(kPairThreads) k_step_pair(const unsigned short *src,
                                                             unsigned short *dst, const StepParams p)
 {
     const int y = blockIdx.y, z = blockIdx.z;
     const bool irow = y > 0 && y < p.ny - 1 && (L::D == 2 || (z > 0 && z < p.nz - 1));
     if (irow || PAT == PAT_LOCAL)
-        pair_body<L, S, PAT, COMP, FORCE, true>(src, dst, p);
+        pair_body<L, S, PAT, COMP, FORCE, true, RED>(src, dst, p);
     else
-        pair_body<L, S, PAT, COMP, FORCE, false>(src, dst, p);
+        pair_body<L, S, PAT, COMP, FORCE, false, RED>(src, dst, p);
 }
 
 }  // namespace lbm

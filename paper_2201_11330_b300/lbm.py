@@ -37,7 +37,7 @@ EXPORTS = [
     "lbm_default_opts", "lbm_tau_from_paper", "lbm_workspace_bytes", "lbm_create",
     "lbm_set_stream", "lbm_init", "lbm_set_force", "lbm_set_lid", "lbm_step",
     "lbm_step_count", "lbm_set_kernel_variant", "lbm_kernel_variant_in_use",
-    "lbm_macroscopic", "lbm_reduce", "lbm_state_bytes", "lbm_get_state",
+    "lbm_step_reduce", "lbm_macroscopic", "lbm_reduce", "lbm_state_bytes", "lbm_get_state",
     "lbm_set_state", "lbm_adjoint_workspace_bytes", "lbm_adjoint_forward",
     "lbm_adjoint_backward", "lbm_adjoint", "lbm_reduce_state_noalloc", "lbm_error_string",
     "lbm_destroy",
@@ -90,6 +90,7 @@ def load():
         "lbm_kernel_variant_in_use": (ip, [_vp]),
         "lbm_macroscopic": (ip, [_vp, _vp, _vp, ip]),
         "lbm_reduce": (ip, [_vp, _dp]),
+        "lbm_step_reduce": (ip, [_vp, _i64, _dp]),
         "lbm_state_bytes": (_sz, [_vp]),
         "lbm_get_state": (ip, [_vp, _vp, ctypes.POINTER(_i64)]),
         "lbm_set_state": (ip, [_vp, _vp, _i64]),
@@ -173,6 +174,12 @@ def lbm_macroscopic(ctx, p_ptr, u_ptr, out_dtype: int):
 def lbm_reduce(ctx):
     out = (ctypes.c_double * 6)()
     _check(load().lbm_reduce(ctx, out), "lbm_reduce")
+    return list(out)
+
+
+def lbm_step_reduce(ctx, n: int):
+    out = (ctypes.c_double * 6)()
+    _check(load().lbm_step_reduce(ctx, int(n), out), "lbm_step_reduce")
     return list(out)
 
 
@@ -372,6 +379,12 @@ class Lattice:
         """dict(mass, momentum (3,), kinetic_energy, max_speed), FP64."""
         self._sync_stream()
         r = lbm_reduce(self.ctx)
+        return {"mass": r[0], "momentum": r[1:4], "kinetic_energy": r[4], "max_speed": r[5]}
+
+    def step_reduce(self, n=1):
+        """step(n) with the last step also returning the Monitor values (as reduce())."""
+        self._sync_stream()
+        r = lbm_step_reduce(self.ctx, n)
         return {"mass": r[0], "momentum": r[1:4], "kinetic_energy": r[4], "max_speed": r[5]}
 
     def state_bytes(self):

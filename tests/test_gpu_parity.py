@@ -372,3 +372,47 @@ def test_paired_equals_plain_bitwise(lattice, shape, storage, bc):
         a = _staged_run(lattice, shape, bc, storage, aa, steps, "plain", force)
         b = _staged_run(lattice, shape, bc, storage, aa, steps, "paired", force)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), (aa, steps, force)
+
+
+# ---------------------------------------------------------------------------
+# lbm_step_reduce: the monitor fused into the last step kernel
+
+
+@pytest.mark.parametrize("lattice,shape,bc", [("d3q19", (50, 40, 30), "cavity"),
+                                              ("d3q27", (36, 21, 17), "channel"),
+                                              ("d2q9", (130, 67, 1), "periodic"),
+                                              ("d3q19", (301, 9, 7), "cavity")])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s", "bf16s"])
+@pytest.mark.parametrize("aa", [False, True])
+def test_step_reduce_matches_reduce(lattice, shape, bc, storage, aa):
+    from paper_2201_11330_b300.lbm import Lattice
+    Q, d = oracle.dims(lattice)
+    p0, u0 = W.random_smooth_state(*shape, d, amp_u=0.05, seed=71)
+    F = torch.from_numpy(W.fourier_force(*shape, amplitude=2e-5, seed=3, dims=d)).cuda()
+    lid = (0.1, 0.0, 0.0) if bc != "periodic" else (0, 0, 0)
+    outs = []
+    for fused in (False, True):
+        lat = Lattice(lattice, *shape, 0.7, bc, storage=storage, aa=aa, lid=lid, has_force=True)
+        lat.set_force(F)
+        lat.init(torch.from_numpy(p0).cuda(), torch.from_numpy(u0).cuda())
+        for steps in (4, 5):
+            if fused:
+                r = lat.step_reduce(steps)
+            else:
+                lat.step(steps)
+                r = lat.reduce()
+            outs.append(r)
+        outs.append(lat.macroscopic())
+    N = int(np.prod(shape))
+    # same state either way
+    assert torch.equal(outs[2][0], outs[5][0]) and torch.equal(outs[2][1], outs[5][1])
+    # same monitor values, up to the order of summation and the storage
+    # rounding: lbm_reduce reads the stored (rounded) post-collision state,
+    # the fused step uses the populations before they are stored
+    tol = {"f64": 1e-12, "f32": 2e-6, "f16s": 1e-4, "bf16s": 1e-3}[storage]
+    rel = {"f64": 1e-11, "f32": 2e-5, "f16s": 3e-3, "bf16s": 2e-2}[storage]
+    for a, b in ((outs[0], outs[3]), (outs[1], outs[4])):
+        assert abs(a["mass"] - b["mass"]) <= tol * N
+        assert np.allclose(a["momentum"], b["momentum"], rtol=0, atol=tol * N * 0.05)
+        assert abs(a["kinetic_energy"] - b["kinetic_energy"]) <= rel * a["kinetic_energy"]
+        assert abs(a["max_speed"] - b["max_speed"]) <= rel * a["max_speed"]
