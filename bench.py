@@ -156,6 +156,12 @@ def barrier(world):
         dist.barrier()
 
 
+def replica_value(nodes_per_rank, steps, max_ms, world):
+    """Whole-job node updates per second (GLUPS) of `world` independent
+    replicas, timed by the slowest rank."""
+    return world * nodes_per_rank * steps / (max_ms * 1e-3) / 1e9
+
+
 def max_over_ranks(value, world, device):
     if world <= 1:
         return value
@@ -207,7 +213,7 @@ def run_cavity(lattice, n, re, storage, aa, steps, warmup, world, device):
     total, durs, parity = timed_steps(lat, steps, warmup, world)
     total = max_over_ranks(total, world, device)
     N = n ** 3
-    glups = world * N * steps / (total * 1e-3) / 1e9
+    glups = replica_value(N, steps, total, world)
     bytes_per_node = 2 * Q_OF[lattice] * BYTES_OF[storage]
     out = {"glups": glups, "ms_per_step": total / steps, "bytes_per_node": bytes_per_node,
            "nodes": N}
