@@ -82,12 +82,6 @@ typedef struct {
     double rho0;        /* constant density of the incompressible model (> 0) */
     double lid_u[3];    /* moving-wall velocity (ignored for LBM_BC_PERIODIC) */
     int has_force;      /* 1: a body-force field will be set with lbm_set_force */
-    int stochastic_round; /* 16-bit storage: round stored values stochastically
-                             (hardware cvt.rs, random bits from a counter-based hash
-                             of node, direction, step and seed) instead of to nearest;
-                             unbiased, so steady regions do not accumulate a rounding
-                             bias.  Deterministic for a given seed.  Ignored otherwise. */
-    unsigned long long seed; /* seed of the stochastic rounding */
 } lbm_opts;
 
 typedef struct lbm_ctx lbm_ctx;

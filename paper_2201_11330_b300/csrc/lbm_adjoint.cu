@@ -122,13 +122,12 @@ int lbm_adjoint_forward(lbm_ctx *c, int64_t T, int64_t K, void *ws, size_t bytes
             dst = at(ws, a.ckpt_off + a.ckpt_stride * (size_t)(k / K));
         else
             dst = (src == c->f[0]) ? c->f[1] : c->f[0];
-        const int rc = ctx_launch_step(c, src, dst, PAT_PULL, nullptr, c->step + k - 1);
+        const int rc = ctx_launch_step(c, src, dst, PAT_PULL, nullptr);
         if (rc != LBM_OK)
             return rc;
         src = dst;
     }
     c->cur = (src == c->f[0]) ? 0 : 1;
-    c->adj_step0 = c->step;
     c->step += T;
     double r[6];
     const int rc = lbm_reduce(c, r);
@@ -179,8 +178,7 @@ int lbm_adjoint_backward(lbm_ctx *c, void *ws, size_t bytes, double *dJdF, doubl
         for (int64_t k = k0 + 1; k < k1; ++k) {
             void *dst = at(ws, a.rec_off[(k - k0 - 1) % 2]);
             rc = ctx_launch_step(c, src, dst, PAT_PULL,
-                                 at(ws, a.useg_off + a.useg_stride * (size_t)(k - k0)),
-                                 c->adj_step0 + k - 1);
+                                 at(ws, a.useg_off + a.useg_stride * (size_t)(k - k0)));
             if (rc != LBM_OK)
                 return rc;
             src = dst;

@@ -243,23 +243,15 @@ __device__ __forceinline__ void bulk_node(const typename Sto<S>::T *src, typenam
     }
     R u[3], s_, rho_;
     collide<L, R, COMP, FORCE>(g, F, c, u, s_, rho_);
-    auto encode = [&](auto A_) -> T {
-        constexpr int a = decltype(A_)::value;
-        if constexpr (S == ST_F16S || S == ST_BF16S) {
-            if (p.sr)
-                return enc_sr<S>(g[a], sr_bits((unsigned)n >> 1, a, p.sr_step, p.sr_seed), n);
-        }
-        return Sto<S>::enc(g[a]);
-    };
     if constexpr (PAT == PAT_PULL) {
         SFor<0, Q>::run([&](auto A_) {
             constexpr int a = decltype(A_)::value;
-            st(dst + a * N + n, encode(A_));
+            st(dst + a * N + n, Sto<S>::enc(g[a]));
         });
     } else if constexpr (PAT == PAT_LOCAL) {
         SFor<0, Q>::run([&](auto A_) {
             constexpr int a = decltype(A_)::value;
-            st(dst + opp<L>(a) * N + n, encode(A_));
+            st(dst + opp<L>(a) * N + n, Sto<S>::enc(g[a]));
         });
     } else {
         AxisNbr X, Y, Z;
@@ -271,7 +263,7 @@ __device__ __forceinline__ void bulk_node(const typename Sto<S>::T *src, typenam
             bool wall;
             upstream<L, b>(X, Y, Z, off, wall);  // x + e_a
             T *ptr = wall ? dst + b * N + n : dst + a * N + (n + off);
-            st(ptr, encode(A_));
+            st(ptr, Sto<S>::enc(g[a]));
         });
     }
 }

@@ -146,10 +146,6 @@ void fill_params(lbm_ctx *c)
         fill_lid_terms<D3Q27>(c);
     p.F = c->force;
     p.u_out = nullptr;
-    p.partials = nullptr;
-    p.sr = (c->opts.stochastic_round && c->opts.storage >= LBM_F16S) ? 1u : 0u;
-    p.sr_seed = (unsigned)(c->opts.seed ^ (c->opts.seed >> 32));
-    p.sr_step = 0;
 }
 
 // The staged kernel copies whole 16-byte aligned row segments: nx (hence N)
@@ -211,10 +207,9 @@ Launch ctx_base_launch(const lbm_ctx *c, int kind) { return base_launch(c, kind)
 cudaError_t ctx_dispatch(const lbm_ctx *c, const Launch &l) { return dispatch(c->lattice, l); }
 
 int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u_out,
-                    int64_t step_index, long long *reduce_blocks)
+                    long long *reduce_blocks)
 {
     Launch l = base_launch(c, K_STEP);
-    l.sp.sr_step = (unsigned)step_index;
     l.pattern = pattern;
     l.src = src;
     l.dst = dst;
@@ -427,9 +422,9 @@ int lbm_step(lbm_ctx *c, int64_t n)
         int rc;
         if (c->opts.aa) {
             const int pat = (c->step % 2 == 0) ? PAT_GATHER : PAT_LOCAL;
-            rc = ctx_launch_step(c, c->f[0], c->f[0], pat, nullptr, c->step);
+            rc = ctx_launch_step(c, c->f[0], c->f[0], pat, nullptr);
         } else {
-            rc = ctx_launch_step(c, c->f[c->cur], c->f[1 - c->cur], PAT_PULL, nullptr, c->step);
+            rc = ctx_launch_step(c, c->f[c->cur], c->f[1 - c->cur], PAT_PULL, nullptr);
             if (rc == LBM_OK)
                 c->cur = 1 - c->cur;
         }
@@ -473,9 +468,9 @@ int lbm_step_reduce(lbm_ctx *c, int64_t n, double *out)
     long long nb = 0;
     if (c->opts.aa) {
         const int pat = (c->step % 2 == 0) ? PAT_GATHER : PAT_LOCAL;
-        rc = ctx_launch_step(c, c->f[0], c->f[0], pat, nullptr, c->step, &nb);
+        rc = ctx_launch_step(c, c->f[0], c->f[0], pat, nullptr, &nb);
     } else {
-        rc = ctx_launch_step(c, c->f[c->cur], c->f[1 - c->cur], PAT_PULL, nullptr, c->step, &nb);
+        rc = ctx_launch_step(c, c->f[c->cur], c->f[1 - c->cur], PAT_PULL, nullptr, &nb);
         if (rc == LBM_OK)
             c->cur = 1 - c->cur;
     }

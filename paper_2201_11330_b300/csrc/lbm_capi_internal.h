@@ -36,7 +36,7 @@ struct lbm_ctx {
     unsigned *err;       // error word of the bounded waits (in the workspace)
     lbm::StepParams sp;
     // adjoint run recorded by lbm_adjoint_forward for lbm_adjoint_backward
-    int64_t adj_T, adj_K, adj_step0;
+    int64_t adj_T, adj_K;
     void *adj_ws;
     size_t adj_bytes;
     bool adj_ready;
@@ -45,10 +45,8 @@ struct lbm_ctx {
 namespace lbm {
 lbm::Launch ctx_base_launch(const lbm_ctx *c, int kind);
 cudaError_t ctx_dispatch(const lbm_ctx *c, const lbm::Launch &l);
-// step_index: 0-based index of the step the launch computes (keys the
-// stochastic rounding of 16-bit storage, so recomputation reproduces it)
 int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u_out,
-                    int64_t step_index, long long *reduce_blocks = nullptr);
+                    long long *reduce_blocks = nullptr);
 int ctx_launch_moments(lbm_ctx *c, const void *src, int form, void *p_out, void *u_out,
                        int out_f32, double *partials);
 int ctx_current_form(const lbm_ctx *c);

@@ -52,9 +52,6 @@ struct StepParams {
     Coef<float> cf;
     Coef<double> cd;
     double *partials;  // per-block monitor sums (RED kernels)
-    unsigned sr;       // 16-bit storage: stochastic rounding of stored values
-    unsigned sr_seed;  // generator seed
-    unsigned sr_step;  // index of the step being computed (0-based)
     const float *F;  // body force, d*N component-major (FORCE kernels)
     void *u_out;     // velocity output, d*N component-major, kernel arithmetic type (UOUT)
 };
@@ -412,19 +409,10 @@ __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typenam
     SFor<0, Q>::run([&](auto A_) {
         constexpr int a = decltype(A_)::value;
         constexpr int b = opp<L>(a);
-        T e;
-        if constexpr (S == ST_F16S || S == ST_BF16S) {
-            if (p.sr)
-                e = enc_sr<S>(g[a], sr_bits((unsigned)n >> 1, a, p.sr_step, p.sr_seed), n);
-            else
-                e = Sto<S>::enc(g[a]);
-        } else {
-            e = Sto<S>::enc(g[a]);
-        }
         if constexpr (PAT == PAT_PULL) {
-            st(dst + a * N + n, e);
+            st(dst + a * N + n, Sto<S>::enc(g[a]));
         } else if constexpr (PAT == PAT_LOCAL) {
-            st(dst + b * N + n, e);
+            st(dst + b * N + n, Sto<S>::enc(g[a]));
         } else {
             // push f*_a to x + e_a, whose upstream along -e_b is x
             int off;
@@ -433,9 +421,9 @@ __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typenam
             if (wall) {
                 // bounced: stays at x as the population entering along e_b
                 // (its lid term, if any, is added when it is read)
-                st(dst + b * N + n, e);
+                st(dst + b * N + n, Sto<S>::enc(g[a]));
             } else {
-                st(dst + a * N + (n + off), e);
+                st(dst + a * N + (n + off), Sto<S>::enc(g[a]));
             }
         }
     });

@@ -143,43 +143,4 @@ struct Sto<ST_BF16S> {
     __device__ __forceinline__ static T enc(R v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
 };
 
-// ---- stochastic rounding of 16-bit storage (optional) -------------------------
-// Random bits from a counter-based generator: the "lowbias32" integer hash
-// (C. Wellons, hash-prospector, 2018) of (node pair, direction, step, seed).
-// The pair (n, n+1), n even, shares one 32-bit word: node n uses its low 16
-// bits, node n+1 its high 16 bits, so the one-node-per-thread and the
-// two-node-per-thread kernels draw the same bits for the same population.
-__device__ __forceinline__ unsigned lowbias32(unsigned x)
-{
-    x ^= x >> 16;
-    x *= 0x7feb352du;
-    x ^= x >> 15;
-    x *= 0x846ca68bu;
-    x ^= x >> 16;
-    return x;
-}
-__device__ __forceinline__ unsigned sr_bits(unsigned pair, int a, unsigned step, unsigned seed)
-{
-    return lowbias32(lowbias32(pair ^ seed) + step * 0x9e3779b9u + (unsigned)a * 0x632be5abu);
-}
-// cvt.rs: round-to-nearest replaced by stochastic rounding driven by rbits
-// (low half <- rbits[15:0], high half <- rbits[31:16]).
-template <int S>
-__device__ __forceinline__ unsigned cvt_rs2(float lo, float hi, unsigned rbits)
-{
-    unsigned d;
-    if constexpr (S == ST_F16S)
-        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
-    else
-        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
-    return d;
-}
-// one value of node n: the half of the pair word that node n owns
-template <int S>
-__device__ __forceinline__ unsigned short enc_sr(float v, unsigned rbits, unsigned n)
-{
-    const unsigned d = cvt_rs2<S>(v, v, rbits);
-    return (unsigned short)((n & 1u) ? (d >> 16) : (d & 0xffffu));
-}
-
 }  // namespace lbm

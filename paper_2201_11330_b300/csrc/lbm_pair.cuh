@@ -350,18 +350,10 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
         }
         float2 u2[3], s2, rho2;
         collide2<L, COMP, FORCE>(g, F, c, u2, s2, rho2);
-        if (p.sr) {
-            const unsigned pair = (unsigned)(n >> 1);
-            SFor<0, Q>::run([&](auto A_) {
-                constexpr int a = decltype(A_)::value;
-                W[a] = cvt_rs2<S>(g[a].x, g[a].y, sr_bits(pair, a, p.sr_step, p.sr_seed));
-            });
-        } else {
-            SFor<0, Q>::run([&](auto A_) {
-                constexpr int a = decltype(A_)::value;
-                W[a] = enc2<S>(g[a]);
-            });
-        }
+        SFor<0, Q>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            W[a] = enc2<S>(g[a]);
+        });
         if constexpr (RED) {  // the two nodes' monitor values, summed in the thread
             float m0[6], m1[6];
             const float ua[3] = {u2[0].x, u2[1].x, u2[2].x}, ub[3] = {u2[0].y, u2[1].y, u2[2].y};

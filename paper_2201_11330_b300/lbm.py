@@ -47,8 +47,7 @@ EXPORTS = [
 class lbm_opts(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("aa", ctypes.c_int), ("compressible", ctypes.c_int),
                 ("f32_unshifted", ctypes.c_int), ("rho0", ctypes.c_double),
-                ("lid_u", ctypes.c_double * 3), ("has_force", ctypes.c_int),
-                ("stochastic_round", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
+                ("lid_u", ctypes.c_double * 3), ("has_force", ctypes.c_int)]
 
 
 class LBMError(RuntimeError):
@@ -263,8 +262,7 @@ class Lattice:
 
     def __init__(self, lattice, nx, ny, nz, tau, bc, *, storage="f32", aa=False,
                  compressible=False, f32_unshifted=False, rho0=1.0, lid=(0.0, 0.0, 0.0),
-                 has_force=False, kernel="auto", stochastic_round=False, seed=0,
-                 device="cuda"):
+                 has_force=False, kernel="auto", device="cuda"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the LBM library needs a CUDA device")
@@ -286,8 +284,6 @@ class Lattice:
         for k in range(3):
             o.lid_u[k] = float(lid[k])
         o.has_force = int(bool(has_force))
-        o.stochastic_round = int(bool(stochastic_round))
-        o.seed = int(seed)
         self.opts = o
         nbytes = lbm_workspace_bytes(self.lattice, nx, ny, nz, o)
         if nbytes == 0:
