@@ -74,6 +74,16 @@ typedef enum {
     LBM_BF16S = 3  /* bfloat16 of f - t, round to nearest even */
 } lbm_storage;
 
+/* Collision operator.  BGK is the paper's (Eq. (collision)); TRT (two
+ * relaxation times, not in the paper) relaxes the symmetric part of each
+ * opposite pair at omega = 1/tau and the antisymmetric part at omega_m set
+ * by the "magic" parameter Lambda = (tau - 1/2)(1/omega_m - 1/2); with
+ * Lambda = 3/16 half-way bounce-back places Poiseuille walls exactly for
+ * any tau, and Lambda = (tau - 1/2)^2 is BGK.  TRT is available with the
+ * incompressible equilibrium only (compressible + TRT is LBM_ERR_ARG) and
+ * has no adjoint. */
+typedef enum { LBM_COLL_BGK = 0, LBM_COLL_TRT = 1 } lbm_collision;
+
 typedef struct {
     int storage;        /* lbm_storage */
     int aa;             /* 0: two-lattice pull scheme; 1: single-lattice AA pattern */
@@ -82,11 +92,14 @@ typedef struct {
     double rho0;        /* constant density of the incompressible model (> 0) */
     double lid_u[3];    /* moving-wall velocity (ignored for LBM_BC_PERIODIC) */
     int has_force;      /* 1: a body-force field will be set with lbm_set_force */
+    int collision;      /* lbm_collision (default BGK) */
+    double trt_lambda;  /* TRT magic parameter (> 0), e.g. 3/16 */
 } lbm_opts;
 
 typedef struct lbm_ctx lbm_ctx;
 
-/* Defaults: LBM_F32, pull scheme, incompressible, shifted, rho0 = 1, lid 0. */
+/* Defaults: LBM_F32, pull scheme, incompressible, BGK, shifted, rho0 = 1,
+ * lid 0, trt_lambda 3/16 (used only with LBM_COLL_TRT). */
 void lbm_default_opts(lbm_opts *opts);
 
 /* tau_std = tau_paper + 1/2 (Sec. 3.3: "ome = 1/(tau+0.5)"). */
@@ -188,7 +201,7 @@ int lbm_set_state(lbm_ctx *ctx, const void *src, int64_t step);
 /* Adjoint (not in the paper): gradients of J = rho0/2 sum_x |u(x, T)|^2
  * after T steps from the current state, with respect to the force field and
  * the moving-wall velocity.  States are checkpointed every K steps and
- * recomputed in between.  Incompressible model and pull scheme only.
+ * recomputed in between.  Incompressible model, BGK and pull scheme only.
  * adj_workspace: device, lbm_adjoint_workspace_bytes(ctx, T, K) bytes.
  * lbm_adjoint_forward runs the T forward steps (the context ends at step
  * T) and returns J; lbm_adjoint_backward then fills dJdF (device FP64, d*N,

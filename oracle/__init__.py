@@ -49,10 +49,11 @@ def _load():
         lib.or_equilibrium.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, dp, dp]
         lib.or_collide_node.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                                        ctypes.c_double, dp, dp, dp]
+                                        ctypes.c_double, dp, dp, dp, ctypes.c_double]
         lib.or_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                               dp, dp, dp, dp, ctypes.c_long, dp, dp, dp, ctypes.c_int]
+                               dp, dp, dp, dp, ctypes.c_long, dp, dp, dp, ctypes.c_int,
+                               ctypes.c_double]
         lib.or_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp, dp,
                                    dp, ctypes.c_long, ctypes.c_long, dp, dp, dp, ctypes.c_int]
@@ -121,8 +122,11 @@ def equilibrium(lattice, P, u, rho0=1.0, compressible=False):
     return out
 
 
-def collide_node(lattice, f, tau, rho0=1.0, compressible=False, F=None):
-    """Eq. (collision) at one node (with the Guo source when F is given)."""
+def collide_node(lattice, f, tau, rho0=1.0, compressible=False, F=None, trt_lambda=None):
+    """Eq. (collision) at one node (with the Guo source when F is given).
+
+    ``trt_lambda`` selects the two-relaxation-time collision with that magic
+    parameter instead of BGK."""
     lib = _load()
     Q, _ = dims(lattice)
     f = _f64(f, Q)
@@ -132,17 +136,18 @@ def collide_node(lattice, f, tau, rho0=1.0, compressible=False, F=None):
         F3 = np.zeros(3)
         F3[: len(F)] = F
     rc = lib.or_collide_node(_lat(lattice), float(tau), int(bool(compressible)), float(rho0),
-                             _dp(f), _dp(F3), _dp(out))
+                             _dp(f), _dp(F3), _dp(out), float(trt_lambda or 0.0))
     assert rc == 0
     return out
 
 
 def run(lattice, nx, ny, nz, tau, bc, steps, *, rho0=1.0, compressible=False, lid=None,
-        F=None, p0=None, u0=None, want_f=False, threads=0):
+        F=None, p0=None, u0=None, want_f=False, threads=0, trt_lambda=None):
     """Forward run of Sec. 3.1's loop for ``steps`` steps.
 
     Returns ``(p, u)`` (or ``(p, u, f)``): p shape (N,), u shape (d, N),
     f shape (Q, N) post-propagation.  ``threads=0`` leaves OpenMP's default.
+    ``trt_lambda`` selects the two-relaxation-time collision.
     """
     lib = _load()
     Q, d = dims(lattice)
@@ -156,7 +161,7 @@ def run(lattice, nx, ny, nz, tau, bc, steps, *, rho0=1.0, compressible=False, li
     f = np.zeros(Q * N) if want_f else None
     rc = lib.or_run(_lat(lattice), nx, ny, nz, float(tau), _bc(bc), int(bool(compressible)),
                     float(rho0), _dp(lid3), _dp(F), _dp(p0), _dp(u0), int(steps), _dp(p),
-                    _dp(u), _dp(f), int(threads))
+                    _dp(u), _dp(f), int(threads), float(trt_lambda or 0.0))
     if rc != 0:
         raise ValueError(f"or_run failed with status {rc}")
     u = u.reshape(d, N)

@@ -36,6 +36,11 @@
  *     form, source (1 - omega/2) t_a [(e_a - u).F/c_s^2 + (e_a.u)(e_a.F)/c_s^4].
  *   - adjoint (not in the paper): the exact transpose of one step, objective
  *     J = rho0/2 sum_x |u(x, T)|^2.
+ *   - two-relaxation-time collision (not in the paper; Ginzburg's TRT): the
+ *     pair halves f+ = (f_a + f_abar)/2 and f- = (f_a - f_abar)/2 relax at
+ *     omega and omega_m, Lambda = (1/omega - 1/2)(1/omega_m - 1/2); the Guo
+ *     source splits the same way, its even half scaled by (1 - omega/2), its
+ *     odd half by (1 - omega_m/2).  Lambda = 0 selects BGK.
  *
  * Pins (tests under tests/ check these against closed forms, conservation
  * laws, analytic flows and finite differences): tables, equilibrium moments,
@@ -80,6 +85,7 @@ typedef struct {
     int lid_on;
     double lid[3];
     double omega, rho0;
+    double omega_m; /* TRT odd-part rate; 0 = BGK */
     int compressible;
     const double *F; /* d*N, component-major, or NULL */
 } or_model;
@@ -219,6 +225,39 @@ static void load_force(const or_model *m, long n, double Fn[3])
         Fn[k] = m->F[(long)k * m->N + n];
 }
 
+/* TRT collision (not in the paper): with g+ = (g_a + g_abar)/2 and
+ * g- = (g_a - g_abar)/2 for g = f, feq and the Guo source S,
+ *     f*_a = f_a - omega (f+ - feq+) - omega_m (f- - feq-)
+ *            + (1 - omega/2) S+ + (1 - omega_m/2) S-.
+ * Overwrites out[] (the BGK result) with this. */
+static void guo_source(const or_dvm *v, int a, const double u[3], const double *Fn, double *S)
+{
+    *S = 0.0;
+    if (!Fn)
+        return;
+    double eu = v->e[a][0] * u[0] + v->e[a][1] * u[1] + v->e[a][2] * u[2];
+    double eF = v->e[a][0] * Fn[0] + v->e[a][1] * Fn[1] + v->e[a][2] * Fn[2];
+    double uF = u[0] * Fn[0] + u[1] * Fn[1] + u[2] * Fn[2];
+    *S = v->t[a] * ((eF - uF) * INV_CS2 + eu * eF * INV_CS2 * INV_CS2);
+}
+
+static void collide_node_trt(const or_model *m, const double *fn, const double *Fn,
+                             const double *feq, const double u[3], double *out)
+{
+    const or_dvm *v = &m->v;
+    for (int a = 0; a < v->Q; ++a) {
+        int b = v->opp[a];
+        double Sa, Sb;
+        guo_source(v, a, u, Fn, &Sa);
+        guo_source(v, b, u, Fn, &Sb);
+        double fp = 0.5 * (fn[a] + fn[b]), fm = 0.5 * (fn[a] - fn[b]);
+        double ep = 0.5 * (feq[a] + feq[b]), em = 0.5 * (feq[a] - feq[b]);
+        double sp = 0.5 * (Sa + Sb), sm = 0.5 * (Sa - Sb);
+        out[a] = fn[a] - m->omega * (fp - ep) - m->omega_m * (fm - em)
+                 + (1.0 - 0.5 * m->omega) * sp + (1.0 - 0.5 * m->omega_m) * sm;
+    }
+}
+
 /* Eq. (collision): f*_a = f_a - omega (f_a - feq_a), omega = 1/(tau_p + 1/2)
  * = 1/tau_std, plus the Guo source in the same trapezoidal form. */
 static void collide_node(const or_model *m, const double *fn, const double *Fn,
@@ -239,6 +278,8 @@ static void collide_node(const or_model *m, const double *fn, const double *Fn,
         }
         out[a] = fn[a] - m->omega * (fn[a] - feq[a]) + src_fac * S;
     }
+    if (m->omega_m > 0.0)
+        collide_node_trt(m, fn, Fn, feq, u, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -345,7 +386,8 @@ static void init_equilibrium(const or_model *m, const double *p0, const double *
 }
 
 static int setup_model(or_model *m, int lattice, int nx, int ny, int nz, double tau, int bc,
-                       int compressible, double rho0, const double *lid, const double *F)
+                       int compressible, double rho0, const double *lid, const double *F,
+                       double trt_lambda)
 {
     memset(m, 0, sizeof(*m));
     if (build_dvm(lattice, &m->v) != OR_OK)
@@ -367,6 +409,10 @@ static int setup_model(or_model *m, int lattice, int nx, int ny, int nz, double 
     for (int k = 0; k < 3; ++k)
         m->lid[k] = lid ? lid[k] : 0.0;
     m->omega = 1.0 / tau;
+    if (!(trt_lambda >= 0.0))
+        return OR_ERR_ARG;
+    if (trt_lambda > 0.0) /* Lambda = (tau - 1/2)(1/omega_m - 1/2) */
+        m->omega_m = 1.0 / (trt_lambda / (tau - 0.5) + 0.5);
     m->rho0 = rho0;
     m->compressible = compressible;
     m->F = F;
@@ -392,10 +438,11 @@ static void set_threads(int nthreads)
 int or_run(int lattice, int nx, int ny, int nz, double tau, int bc, int compressible,
            double rho0, const double *lid, const double *F, const double *p0,
            const double *u0, long nsteps, double *p_out, double *u_out, double *f_out,
-           int nthreads)
+           int nthreads, double trt_lambda)
 {
     or_model m;
-    int rc = setup_model(&m, lattice, nx, ny, nz, tau, bc, compressible, rho0, lid, F);
+    int rc = setup_model(&m, lattice, nx, ny, nz, tau, bc, compressible, rho0, lid, F,
+                         trt_lambda);
     if (rc != OR_OK || nsteps < 0)
         return OR_ERR_ARG;
     set_threads(nthreads);
@@ -424,11 +471,11 @@ int or_run(int lattice, int nx, int ny, int nz, double tau, int bc, int compress
 
 /* Exported: one collision at one node (tiny brute-force pins). */
 int or_collide_node(int lattice, double tau, int compressible, double rho0, const double *fn,
-                    const double *F3, double *out)
+                    const double *F3, double *out, double trt_lambda)
 {
     or_model m;
     int rc = setup_model(&m, lattice, 1, 1, 1, tau, OR_BC_PERIODIC, compressible, rho0, NULL,
-                         NULL);
+                         NULL, trt_lambda);
     if (rc != OR_OK)
         return rc;
     collide_node(&m, fn, F3, out);
@@ -564,7 +611,7 @@ int or_adjoint(int lattice, int nx, int ny, int nz, double tau, int bc, double r
                long T, long K, double *J_out, double *dJdF, double *dJdU, int nthreads)
 {
     or_model m;
-    int rc = setup_model(&m, lattice, nx, ny, nz, tau, bc, 0, rho0, lid, F);
+    int rc = setup_model(&m, lattice, nx, ny, nz, tau, bc, 0, rho0, lid, F, 0.0);
     if (rc != OR_OK || T < 1 || K < 1)
         return OR_ERR_ARG;
     set_threads(nthreads);

@@ -33,7 +33,10 @@ struct AdjLayout {
     size_t real;  // bytes of the adjoint arithmetic type
 };
 
-bool adj_supported(const lbm_ctx *c) { return !c->opts.aa && !c->opts.compressible; }
+bool adj_supported(const lbm_ctx *c)
+{
+    return !c->opts.aa && !c->opts.compressible && c->opts.collision == LBM_COLL_BGK;
+}
 
 AdjLayout adj_layout(const lbm_ctx *c, int64_t T, int64_t K)
 {

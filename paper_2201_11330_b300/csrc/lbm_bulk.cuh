@@ -175,7 +175,7 @@ __device__ __forceinline__ void bulk_issue(const typename Sto<S>::T *src, typena
 }
 
 // One node of a staged segment.  IROW: the row is interior in y and z.
-template <class L, int S, int PAT, bool COMP, bool FORCE, bool IROW>
+template <class L, int S, int PAT, int MODEL, bool FORCE, bool IROW>
 __device__ __forceinline__ void bulk_node(const typename Sto<S>::T *src, typename Sto<S>::T *dst,
                                           typename Sto<S>::T *sb, const StepParams &p, int x0,
                                           int y, int z, int tid)
@@ -242,7 +242,7 @@ __device__ __forceinline__ void bulk_node(const typename Sto<S>::T *src, typenam
         });
     }
     R u[3], s_, rho_;
-    collide<L, R, COMP, FORCE>(g, F, c, u, s_, rho_);
+    collide<L, R, MODEL, FORCE>(g, F, c, u, s_, rho_);
     if constexpr (PAT == PAT_PULL) {
         SFor<0, Q>::run([&](auto A_) {
             constexpr int a = decltype(A_)::value;
@@ -268,7 +268,7 @@ __device__ __forceinline__ void bulk_node(const typename Sto<S>::T *src, typenam
     }
 }
 
-template <class L, int S, int PAT, bool COMP, bool FORCE>
+template <class L, int S, int PAT, int MODEL, bool FORCE>
 __global__ void __launch_bounds__(kBulkSeg) k_step_bulk(const typename Sto<S>::T *src,
                                                         typename Sto<S>::T *dst, const StepParams p,
                                                         const BulkParams bp)
@@ -318,9 +318,9 @@ __global__ void __launch_bounds__(kBulkSeg) k_step_bulk(const typename Sto<S>::T
         if (x0 + tid < p.nx) {
             const bool irow = y > 0 && y < p.ny - 1 && (L::D == 2 || (z > 0 && z < p.nz - 1));
             if (irow)
-                bulk_node<L, S, PAT, COMP, FORCE, true>(src, dst, sb, p, x0, y, z, tid);
+                bulk_node<L, S, PAT, MODEL, FORCE, true>(src, dst, sb, p, x0, y, z, tid);
             else
-                bulk_node<L, S, PAT, COMP, FORCE, false>(src, dst, sb, p, x0, y, z, tid);
+                bulk_node<L, S, PAT, MODEL, FORCE, false>(src, dst, sb, p, x0, y, z, tid);
         }
         __syncthreads();  // every read of stage s is done
         if (tid == 0) {

@@ -48,6 +48,11 @@ bool valid_opts(const lbm_opts &o)
 {
     if (o.storage < LBM_F64 || o.storage > LBM_BF16S)
         return false;
+    if (o.collision != LBM_COLL_BGK && o.collision != LBM_COLL_TRT)
+        return false;
+    if (o.collision == LBM_COLL_TRT &&
+        (o.compressible || !(o.trt_lambda > 0.0 && isfinite(o.trt_lambda))))
+        return false;
     if (!(o.rho0 > 0.0) || !isfinite(o.rho0))
         return false;
     for (int k = 0; k < 3; ++k)
@@ -124,6 +129,13 @@ void fill_params(lbm_ctx *c)
     p.lid_on = c->bc != LBM_BC_PERIODIC;
     const double omega = 1.0 / c->tau;
     const double sigma = c->shifted ? 1.0 : 0.0;
+    // TRT: Lambda = (1/omega - 1/2)(1/omega_m - 1/2); BGK: omega_m = omega
+    const double omega_m =
+        c->opts.collision == LBM_COLL_TRT ? 1.0 / (c->opts.trt_lambda / (c->tau - 0.5) + 0.5) : omega;
+    p.cd.omega_m = omega_m;
+    p.cd.kf_m = (1.0 - 0.5 * omega_m) / omega_m;
+    p.cf.omega_m = (float)omega_m;
+    p.cf.kf_m = (float)p.cd.kf_m;
     p.cd.omega = omega;
     p.cd.rho0 = c->opts.rho0;
     p.cd.inv_rho0 = 1.0 / c->opts.rho0;
@@ -188,6 +200,7 @@ Launch base_launch(const lbm_ctx *c, int kind)
     l.kind = kind;
     l.storage = c->opts.storage;
     l.comp = c->opts.compressible != 0;
+    l.model = l.comp ? M_COMP : c->opts.collision == LBM_COLL_TRT ? M_TRT : M_INC;
     l.force = c->force != nullptr;
     l.uout = false;
     l.sp = c->sp;
@@ -279,6 +292,8 @@ void lbm_default_opts(lbm_opts *o)
     memset(o, 0, sizeof(*o));
     o->storage = LBM_F32;
     o->rho0 = 1.0;
+    o->collision = LBM_COLL_BGK;
+    o->trt_lambda = 3.0 / 16.0;
 }
 
 double lbm_tau_from_paper(double tau_paper) { return tau_paper + 0.5; }

@@ -27,6 +27,9 @@
 namespace lbm {
 
 enum Pattern { PAT_PULL = 0, PAT_GATHER = 1, PAT_LOCAL = 2 };
+// Collision model of a step kernel: incompressible BGK (the paper's),
+// compressible BGK, incompressible two-relaxation-time.
+enum Model { M_INC = 0, M_COMP = 1, M_TRT = 2 };
 // Where post-collision populations f*_a(x) sit in the stored state.
 enum Form { FORM_LOCAL = 0, FORM_SWAPPED = 1, FORM_STREAMED = 2 };
 
@@ -41,6 +44,8 @@ struct Coef {
     R inv_rho0;  // 1/rho0
     R sigma;     // 1 when the storage holds f - t, else 0
     R kf;        // (1 - omega/2)/omega: force source folded into the equilibrium
+    R omega_m;   // TRT: relaxation rate of the antisymmetric part
+    R kf_m;      // TRT: (1 - omega_m/2)/omega_m
     R lid[kMaxQ];  // 2 t_a rho0 (e_a . U)/c_s^2 for links crossing the moving wall
 };
 
@@ -111,10 +116,11 @@ __device__ __forceinline__ double o_fma(double a, double b, double c) { return _
 // equilibrium as kf*S_a, and opposite directions are handled in pairs:
 //   feq_a = t_a [A + 4.5 rho (e.u)^2] +/- t_a 3 rho (e.u),
 //   A = sum g - 1.5 rho u.u  (the sigma*t_a shift cancels).
-template <class L, class R, bool COMP, bool FORCE>
+template <class L, class R, int MODEL, bool FORCE>
 __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coef<R> &c,
                                         R (&u)[3], R &s_out, R &rho_out)
 {
+    constexpr bool COMP = MODEL == M_COMP;
     constexpr int H = L::Q / 2;
     R sp[H], sm[H];
     SFor<0, H>::run([&](auto A_) {
@@ -162,10 +168,10 @@ __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coe
     }
     const R r3 = o_mul(R(3), rho), r45 = o_mul(R(4.5), rho);
     const R om = c.omega;
-    SFor<0, H>::run([&](auto A_) {
+    // equilibrium (+ folded source) of pair a: symmetric and antisymmetric
+    // parts, feq_a = t (sym + asym), feq_b = t (sym - asym)
+    auto pair_eq = [&](auto A_, R &sym, R &asym) {
         constexpr int a = decltype(A_)::value;
-        constexpr int b = opp<L>(a);
-        const R t = R(L::w(a));
         // e.u = (e.j') ir with j' = j (+ F/2): sums first, one product last
         R ej = R(0), eF = R(0);
         (void)eF;
@@ -182,19 +188,46 @@ __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coe
             }
         });
         const R eu = o_mul(ej, ir);
-        R sym = o_fma(o_mul(r45, eu), eu, A);
-        R asym = o_mul(r3, eu);
+        sym = o_fma(o_mul(r45, eu), eu, A);
+        asym = o_mul(r3, eu);
         if constexpr (FORCE) {
             sym = o_fma(o_mul(o_mul(R(9), c.kf), eu), eF, sym);
-            asym = o_fma(o_mul(R(3), c.kf), eF, asym);
+            asym = o_fma(o_mul(R(3), MODEL == M_TRT ? c.kf_m : c.kf), eF, asym);
         }
-        // no product feeds an add directly: each multiply-add is one
-        // explicit fma, so no compiler can fuse (and re-round) it differently
-        const R at = o_mul(asym, t);
-        const R fa = o_fma(sym, t, at), fb = o_fma(sym, t, -at);
-        g[a] = o_fma(om, o_sub(fa, g[a]), g[a]);
-        g[b] = o_fma(om, o_sub(fb, g[b]), g[b]);
-    });
+    };
+    if constexpr (MODEL == M_TRT) {
+        // Two relaxation times: the symmetric half-sum (g_a + g_b)/2 relaxes
+        // at omega towards t sym, the antisymmetric half-difference at
+        // omega_m towards t asym; the source's antisymmetric part carries
+        // (1 - omega_m/2).
+        const R omm = c.omega_m;
+        SFor<0, H>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            constexpr int b = opp<L>(a);
+            const R t = R(L::w(a));
+            R sym, asym;
+            pair_eq(A_, sym, asym);
+            const R hp = o_fma(o_add(g[a], g[b]), R(0.5), -o_mul(sym, t));
+            const R hm = o_fma(o_sub(g[a], g[b]), R(0.5), -o_mul(asym, t));
+            g[a] = o_fma(-omm, hm, o_fma(-om, hp, g[a]));
+            g[b] = o_fma(omm, hm, o_fma(-om, hp, g[b]));
+        });
+    } else {
+        SFor<0, H>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            constexpr int b = opp<L>(a);
+            const R t = R(L::w(a));
+            R sym, asym;
+            pair_eq(A_, sym, asym);
+            // no product feeds an add directly: each multiply-add is one
+            // explicit fma, so no compiler can fuse (and re-round) it
+            // differently
+            const R at = o_mul(asym, t);
+            const R fa = o_fma(sym, t, at), fb = o_fma(sym, t, -at);
+            g[a] = o_fma(om, o_sub(fa, g[a]), g[a]);
+            g[b] = o_fma(om, o_sub(fb, g[b]), g[b]);
+        });
+    }
     {
         const R t0 = R(L::w(H));
         g[H] = o_fma(om, o_fma(t0, A, -g[H]), g[H]);
@@ -337,7 +370,7 @@ __device__ __forceinline__ void block_monitor(const R (&mon)[6], double *partial
 // ---- one node of one time step ----------------------------------------------
 // INTERIOR: the node's row has neighbours inside the box in y and z (no wall,
 // no wrap), so only the x axis needs per-thread boundary logic.
-template <class L, int S, int PAT, bool COMP, bool FORCE, bool UOUT, bool INTERIOR,
+template <class L, int S, int PAT, int MODEL, bool FORCE, bool UOUT, bool INTERIOR,
           bool RED = false>
 __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typename Sto<S>::T *dst,
                                           const StepParams &p, int x, int y, int z,
@@ -397,7 +430,7 @@ __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typenam
         });
     }
     R u[3], s_, rho_;
-    collide<L, R, COMP, FORCE>(g, F, c, u, s_, rho_);
+    collide<L, R, MODEL, FORCE>(g, F, c, u, s_, rho_);
     if constexpr (RED)
         monitor_values(s_, rho_, u, mon);
     if constexpr (UOUT) {
@@ -430,7 +463,7 @@ __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typenam
 }
 
 // grid: (ceil(nx/blockDim.x), ny, nz); one node per thread.
-template <class L, int S, int PAT, bool COMP, bool FORCE, bool UOUT, bool RED = false>
+template <class L, int S, int PAT, int MODEL, bool FORCE, bool UOUT, bool RED = false>
 // (__launch_bounds__ with an explicit minimum of 1 block lets nvcc roughly
 // double the register count of these kernels and halves their occupancy;
 // the thread bound alone keeps them at 40-48 registers.)
@@ -447,14 +480,14 @@ __global__ void __launch_bounds__(256) k_step(const typename Sto<S>::T *src,
     R mon[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     if (x < p.nx) {
         if constexpr (PAT == PAT_LOCAL) {
-            step_node<L, S, PAT, COMP, FORCE, UOUT, true, RED>(src, dst, p, x, y, z, mon);
+            step_node<L, S, PAT, MODEL, FORCE, UOUT, true, RED>(src, dst, p, x, y, z, mon);
         } else {
             const bool interior =
                 y > 0 && y < p.ny - 1 && (L::D == 2 || (z > 0 && z < p.nz - 1));
             if (interior)
-                step_node<L, S, PAT, COMP, FORCE, UOUT, true, RED>(src, dst, p, x, y, z, mon);
+                step_node<L, S, PAT, MODEL, FORCE, UOUT, true, RED>(src, dst, p, x, y, z, mon);
             else
-                step_node<L, S, PAT, COMP, FORCE, UOUT, false, RED>(src, dst, p, x, y, z, mon);
+                step_node<L, S, PAT, MODEL, FORCE, UOUT, false, RED>(src, dst, p, x, y, z, mon);
         }
     }
     if constexpr (RED)
@@ -468,7 +501,7 @@ struct InitParams {
     int compressible_unused;
 };
 
-template <class L, int S, bool AA, bool COMP, bool FORCE>
+template <class L, int S, bool AA, int MODEL, bool FORCE>
 __global__ void __launch_bounds__(256) k_init(typename Sto<S>::T *dst, const StepParams p,
                                               const double *p0, const double *u0)
 {
@@ -489,7 +522,7 @@ __global__ void __launch_bounds__(256) k_init(typename Sto<S>::T *dst, const Ste
         for (int k = 0; k < L::D; ++k)
             u[k] = R(u0[k * N + n]);
     const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const R rho = COMP ? R(P) : c.rho0;
+    const R rho = MODEL == M_COMP ? R(P) : c.rho0;
     R g[Q];
     SFor<0, Q>::run([&](auto A_) {
         constexpr int a = decltype(A_)::value;
@@ -504,7 +537,7 @@ __global__ void __launch_bounds__(256) k_init(typename Sto<S>::T *dst, const Ste
         for (int k = 0; k < L::D; ++k)
             F[k] = R(p.F[k * N + n]);
         R uc[3], s_, rho_;
-        collide<L, R, COMP, true>(g, F, c, uc, s_, rho_);
+        collide<L, R, MODEL, true>(g, F, c, uc, s_, rho_);
     }
     SFor<0, Q>::run([&](auto A_) {
         constexpr int a = decltype(A_)::value;
@@ -736,6 +769,7 @@ struct Launch {
     int storage;
     int pattern;  // K_STEP: Pattern; K_MOMENTS: Form; K_INIT: 1 = AA slots
     bool comp, force, uout;
+    int model;  // K_STEP / K_INIT: Model
     const void *src;
     void *dst;
     StepParams sp;

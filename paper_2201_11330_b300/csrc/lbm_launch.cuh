@@ -11,11 +11,11 @@ namespace lbm {
 
 // Persistent launch of the staged kernel: as many blocks as fit on the GPU
 // (queried once per instantiation), never more than there are segments.
-template <class L, int S, int PAT, bool COMP, bool FORCE>
+template <class L, int S, int PAT, int MODEL, bool FORCE>
 cudaError_t launch_bulk(const Launch &l)
 {
     using T = typename Sto<S>::T;
-    auto kern = k_step_bulk<L, S, PAT, COMP, FORCE>;
+    auto kern = k_step_bulk<L, S, PAT, MODEL, FORCE>;
     constexpr size_t smem = bulk_smem_bytes<L, T>();
     static int per_sm = -1;
     if (per_sm < 0) {
@@ -48,6 +48,25 @@ inline cudaError_t with_bool(bool b, F &&f)
     return b ? f(std::true_type{}) : f(std::false_type{});
 }
 
+template <int M>
+using model_c = std::integral_constant<int, M>;
+
+// one instantiation per collision model (Model)
+template <class F>
+inline cudaError_t with_model(int m, F &&f)
+{
+    switch (m) {
+    case M_INC:
+        return f(model_c<M_INC>{});
+    case M_COMP:
+        return f(model_c<M_COMP>{});
+    case M_TRT:
+        return f(model_c<M_TRT>{});
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
 template <class L, int S>
 cudaError_t launch_storage(const Launch &l)
 {
@@ -57,9 +76,10 @@ cudaError_t launch_storage(const Launch &l)
     if (l.kind == K_STEP && l.pair) {
         if constexpr (S == ST_F16S || S == ST_BF16S) {
             const dim3 grid((l.sp.nx + 2 * kPairThreads - 1) / (2 * kPairThreads), l.sp.ny, l.sp.nz);
-            return with_bool(l.comp, [&](auto C) {
+            return with_model(l.model, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
-                    constexpr bool c = decltype(C)::value, fo = decltype(Fo)::value;
+                    constexpr int c = decltype(C)::value;
+                    constexpr bool fo = decltype(Fo)::value;
                     const auto *s16 = (const unsigned short *)l.src;
                     auto *d16 = (unsigned short *)l.dst;
                     return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
@@ -79,9 +99,10 @@ cudaError_t launch_storage(const Launch &l)
         }
     }
     if (l.kind == K_STEP && l.bulk) {
-        return with_bool(l.comp, [&](auto C) {
+        return with_model(l.model, [&](auto C) {
             return with_bool(l.force, [&](auto Fo) {
-                constexpr bool c = decltype(C)::value, fo = decltype(Fo)::value;
+                constexpr int c = decltype(C)::value;
+                constexpr bool fo = decltype(Fo)::value;
                 if (l.pattern == PAT_PULL)
                     return launch_bulk<L, S, PAT_PULL, c, fo>(l);
                 if (l.pattern == PAT_GATHER)
@@ -93,14 +114,14 @@ cudaError_t launch_storage(const Launch &l)
     if (l.kind == K_STEP) {
         if (l.pattern == PAT_PULL) {
             if (l.uout) {
-                // adjoint recompute: incompressible model only
+                // adjoint recompute: incompressible BGK only
                 return with_bool(l.force, [&](auto Fo) {
-                    k_step<L, S, PAT_PULL, false, decltype(Fo)::value, true>
+                    k_step<L, S, PAT_PULL, M_INC, decltype(Fo)::value, true>
                         <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
                     return cudaGetLastError();
                 });
             }
-            return with_bool(l.comp, [&](auto C) {
+            return with_model(l.model, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
                     return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
                         k_step<L, S, PAT_PULL, decltype(C)::value, decltype(Fo)::value, false,
@@ -111,7 +132,7 @@ cudaError_t launch_storage(const Launch &l)
             });
         }
         if (l.pattern == PAT_GATHER) {
-            return with_bool(l.comp, [&](auto C) {
+            return with_model(l.model, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
                     return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
                         k_step<L, S, PAT_GATHER, decltype(C)::value, decltype(Fo)::value, false,
@@ -121,7 +142,7 @@ cudaError_t launch_storage(const Launch &l)
                 });
             });
         }
-        return with_bool(l.comp, [&](auto C) {
+        return with_model(l.model, [&](auto C) {
             return with_bool(l.force, [&](auto Fo) {
                 return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
                     k_step<L, S, PAT_LOCAL, decltype(C)::value, decltype(Fo)::value, false,
@@ -133,7 +154,7 @@ cudaError_t launch_storage(const Launch &l)
     }
     if (l.kind == K_INIT) {
         return with_bool(l.pattern == 1, [&](auto AA) {
-            return with_bool(l.comp, [&](auto C) {
+            return with_model(l.model, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
                     k_init<L, S, decltype(AA)::value, decltype(C)::value, decltype(Fo)::value>
                         <<<l.grid, l.block, 0, l.stream>>>(dst, l.sp, l.p0, l.u0);

@@ -74,11 +74,12 @@ __device__ __forceinline__ float2 v_bc(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float2 v_neg(float2 a) { return make_float2(-a.x, -a.y); }
 
 // collide() of lbm_kernels.cuh on two nodes at once, operation for operation.
-template <class L, bool COMP, bool FORCE>
+template <class L, int MODEL, bool FORCE>
 __device__ __forceinline__ void collide2(float2 (&g)[L::Q], const float2 (&F)[3],
                                          const Coef<float> &c, float2 (&u_out)[3], float2 &s_out,
                                          float2 &rho_out)
 {
+    constexpr bool COMP = MODEL == M_COMP;
     constexpr int H = L::Q / 2;
     float2 sp[H], sm[H];
     SFor<0, H>::run([&](auto A_) {
@@ -126,10 +127,9 @@ __device__ __forceinline__ void collide2(float2 (&g)[L::Q], const float2 (&F)[3]
     }
     const float2 r3 = v_mul(v_bc(3.f), rho), r45 = v_mul(v_bc(4.5f), rho);
     const float2 om = v_bc(c.omega);
-    SFor<0, H>::run([&](auto A_) {
+    // same operations, in the same order, as the scalar collide()
+    auto pair_eq = [&](auto A_, float2 &sym, float2 &asym) {
         constexpr int a = decltype(A_)::value;
-        constexpr int b = opp<L>(a);
-        const float2 t = v_bc(float(L::w(a)));
         float2 ej = v_bc(0.f), eF = v_bc(0.f);
         (void)eF;
         SFor<0, 3>::run([&](auto K_) {
@@ -145,17 +145,39 @@ __device__ __forceinline__ void collide2(float2 (&g)[L::Q], const float2 (&F)[3]
             }
         });
         const float2 eu = v_mul(ej, ir);
-        float2 sym = v_fma(v_mul(r45, eu), eu, A);
-        float2 asym = v_mul(r3, eu);
+        sym = v_fma(v_mul(r45, eu), eu, A);
+        asym = v_mul(r3, eu);
         if constexpr (FORCE) {
             sym = v_fma(v_mul(v_bc(__fmul_rn(9.f, c.kf)), eu), eF, sym);
-            asym = v_fma(v_bc(__fmul_rn(3.f, c.kf)), eF, asym);
+            asym = v_fma(v_bc(__fmul_rn(3.f, MODEL == M_TRT ? c.kf_m : c.kf)), eF, asym);
         }
-        const float2 at = v_mul(asym, t);
-        const float2 fa = v_fma(sym, t, at), fb = v_fma(sym, t, v_neg(at));
-        g[a] = v_fma(om, v_sub(fa, g[a]), g[a]);
-        g[b] = v_fma(om, v_sub(fb, g[b]), g[b]);
-    });
+    };
+    if constexpr (MODEL == M_TRT) {
+        const float2 omm = v_bc(c.omega_m);
+        SFor<0, H>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            constexpr int b = opp<L>(a);
+            const float2 t = v_bc(float(L::w(a)));
+            float2 sym, asym;
+            pair_eq(A_, sym, asym);
+            const float2 hp = v_fma(v_add(g[a], g[b]), v_bc(0.5f), v_neg(v_mul(sym, t)));
+            const float2 hm = v_fma(v_sub(g[a], g[b]), v_bc(0.5f), v_neg(v_mul(asym, t)));
+            g[a] = v_fma(v_neg(omm), hm, v_fma(v_neg(om), hp, g[a]));
+            g[b] = v_fma(omm, hm, v_fma(v_neg(om), hp, g[b]));
+        });
+    } else {
+        SFor<0, H>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            constexpr int b = opp<L>(a);
+            const float2 t = v_bc(float(L::w(a)));
+            float2 sym, asym;
+            pair_eq(A_, sym, asym);
+            const float2 at = v_mul(asym, t);
+            const float2 fa = v_fma(sym, t, at), fb = v_fma(sym, t, v_neg(at));
+            g[a] = v_fma(om, v_sub(fa, g[a]), g[a]);
+            g[b] = v_fma(om, v_sub(fb, g[b]), g[b]);
+        });
+    }
     {
         const float2 t0 = v_bc(float(L::w(H)));
         g[H] = v_fma(om, v_fma(t0, A, v_neg(g[H])), g[H]);
@@ -236,7 +258,7 @@ __device__ __forceinline__ int shifted_row(const StepParams &p, int y, int z, bo
     return ys + p.ny * zs;
 }
 
-template <class L, int S, int PAT, bool COMP, bool FORCE, bool IROW, bool RED>
+template <class L, int S, int PAT, int MODEL, bool FORCE, bool IROW, bool RED>
 __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned short *dst,
                                           const StepParams &p)
 {
@@ -349,7 +371,7 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
                 F[k] = *reinterpret_cast<const float2 *>(p.F + k * N + n);
         }
         float2 u2[3], s2, rho2;
-        collide2<L, COMP, FORCE>(g, F, c, u2, s2, rho2);
+        collide2<L, MODEL, FORCE>(g, F, c, u2, s2, rho2);
         SFor<0, Q>::run([&](auto A_) {
             constexpr int a = decltype(A_)::value;
             W[a] = enc2<S>(g[a]);
@@ -434,16 +456,16 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
         block_monitor(mon, p.partials);
 }
 
-template <class L, int S, int PAT, bool COMP, bool FORCE, bool RED = false>
+template <class L, int S, int PAT, int MODEL, bool FORCE, bool RED = false>
 __global__ void __launch_bounds__(kPairThreads) k_step_pair(const unsigned short *src,
                                                             unsigned short *dst, const StepParams p)
 {
     const int y = blockIdx.y, z = blockIdx.z;
     const bool irow = y > 0 && y < p.ny - 1 && (L::D == 2 || (z > 0 && z < p.nz - 1));
     if (irow || PAT == PAT_LOCAL)
-        pair_body<L, S, PAT, COMP, FORCE, true, RED>(src, dst, p);
+        pair_body<L, S, PAT, MODEL, FORCE, true, RED>(src, dst, p);
     else
-        pair_body<L, S, PAT, COMP, FORCE, false, RED>(src, dst, p);
+        pair_body<L, S, PAT, MODEL, FORCE, false, RED>(src, dst, p);
 }
 
 }  // namespace lbm

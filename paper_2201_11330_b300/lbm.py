@@ -23,6 +23,7 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_STATE, LBM_ERR_NOME
 LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 = 0, 1, 2
 LBM_BC_PERIODIC, LBM_BC_CAVITY, LBM_BC_CHANNEL = 0, 1, 2
 LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = 0, 1, 2, 3
+LBM_COLL_BGK, LBM_COLL_TRT = 0, 1
 LBM_KERNEL_AUTO, LBM_KERNEL_PLAIN, LBM_KERNEL_STAGED, LBM_KERNEL_PAIRED = 0, 1, 2, 3
 KERNELS = {"auto": LBM_KERNEL_AUTO, "plain": LBM_KERNEL_PLAIN, "staged": LBM_KERNEL_STAGED,
            "paired": LBM_KERNEL_PAIRED}
@@ -47,7 +48,8 @@ EXPORTS = [
 class lbm_opts(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("aa", ctypes.c_int), ("compressible", ctypes.c_int),
                 ("f32_unshifted", ctypes.c_int), ("rho0", ctypes.c_double),
-                ("lid_u", ctypes.c_double * 3), ("has_force", ctypes.c_int)]
+                ("lid_u", ctypes.c_double * 3), ("has_force", ctypes.c_int),
+                ("collision", ctypes.c_int), ("trt_lambda", ctypes.c_double)]
 
 
 class LBMError(RuntimeError):
@@ -262,7 +264,7 @@ class Lattice:
 
     def __init__(self, lattice, nx, ny, nz, tau, bc, *, storage="f32", aa=False,
                  compressible=False, f32_unshifted=False, rho0=1.0, lid=(0.0, 0.0, 0.0),
-                 has_force=False, kernel="auto", device="cuda"):
+                 has_force=False, kernel="auto", trt_lambda=None, device="cuda"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the LBM library needs a CUDA device")
@@ -284,6 +286,9 @@ class Lattice:
         for k in range(3):
             o.lid_u[k] = float(lid[k])
         o.has_force = int(bool(has_force))
+        if trt_lambda is not None:  # two-relaxation-time collision
+            o.collision = LBM_COLL_TRT
+            o.trt_lambda = float(trt_lambda)
         self.opts = o
         nbytes = lbm_workspace_bytes(self.lattice, nx, ny, nz, o)
         if nbytes == 0:

@@ -38,6 +38,7 @@ def test_default_opts_and_tau(lib):
     o = lbm.lbm_default_opts()
     assert o.storage == lbm.LBM_F32 and o.aa == 0 and o.compressible == 0
     assert o.rho0 == 1.0 and list(o.lid_u) == [0.0, 0.0, 0.0]
+    assert o.collision == lbm.LBM_COLL_BGK and o.trt_lambda == 3 / 16
     assert lbm.lbm_tau_from_paper(0.3) == 0.8
     assert lbm.lbm_error_string(lbm.LBM_ERR_ARG) == "invalid argument"
     assert lbm.lbm_error_string(12345) == "unknown status"
@@ -85,6 +86,17 @@ def test_create_validates_before_touching_memory(lib):
     o = lbm.lbm_default_opts()
     o.rho0 = -1.0
     assert _create(lib, opts=o)[0] == lbm.LBM_ERR_ARG
+    # two-relaxation-time collision: Lambda > 0, incompressible model only
+    o = lbm.lbm_default_opts()
+    o.collision = 7
+    assert _create(lib, opts=o)[0] == lbm.LBM_ERR_ARG
+    o.collision = lbm.LBM_COLL_TRT
+    for lam in (0.0, -0.1, float("inf"), float("nan")):
+        o.trt_lambda = lam
+        assert _create(lib, opts=o)[0] == lbm.LBM_ERR_ARG
+    o.trt_lambda = 3 / 16
+    o.compressible = 1
+    assert _create(lib, opts=o)[0] == lbm.LBM_ERR_ARG
 
 
 def test_state_machine_errors_without_launch(lib):
@@ -104,6 +116,14 @@ def test_state_machine_errors_without_launch(lib):
         assert lib.lbm_set_lid(ctx, bad) == lbm.LBM_ERR_ARG
         assert lib.lbm_state_bytes(ctx) == 19 * 512 * 4
         assert lib.lbm_adjoint_workspace_bytes(ctx, 0, 1) == 0
+    finally:
+        lib.lbm_destroy(ctx)
+    o = lbm.lbm_default_opts()
+    o.collision = lbm.LBM_COLL_TRT
+    rc, ctx = _create(lib, opts=o)
+    assert rc == lbm.LBM_OK
+    try:  # the adjoint covers BGK only
+        assert lib.lbm_adjoint_workspace_bytes(ctx, 10, 2) == 0
     finally:
         lib.lbm_destroy(ctx)
     assert lib.lbm_step_count(None) == -1

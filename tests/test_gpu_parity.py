@@ -27,12 +27,14 @@ def _need_gpu():
 
 
 def gpu_run(lattice, shape, tau, bc, steps, *, storage="f64", aa=False, lid=None, F=None,
-            p0=None, u0=None, compressible=False, rho0=1.0, f32_unshifted=False):
+            p0=None, u0=None, compressible=False, rho0=1.0, f32_unshifted=False,
+            trt_lambda=None, kernel="auto"):
     from paper_2201_11330_b300.lbm import Lattice
     nx, ny, nz = shape
     lat = Lattice(lattice, nx, ny, nz, tau, bc, storage=storage, aa=aa,
                   compressible=compressible, rho0=rho0, lid=lid or (0, 0, 0),
-                  has_force=F is not None, f32_unshifted=f32_unshifted)
+                  has_force=F is not None, f32_unshifted=f32_unshifted,
+                  trt_lambda=trt_lambda, kernel=kernel)
     if F is not None:
         lat.set_force(torch.from_numpy(np.ascontiguousarray(F, dtype=np.float32)).cuda())
     lat.init(None if p0 is None else torch.from_numpy(p0).cuda(),
@@ -45,12 +47,12 @@ def gpu_run(lattice, shape, tau, bc, steps, *, storage="f64", aa=False, lid=None
 
 
 def oracle_run(lattice, shape, tau, bc, steps, *, lid=None, F=None, p0=None, u0=None,
-               compressible=False, rho0=1.0):
+               compressible=False, rho0=1.0, trt_lambda=None):
     nx, ny, nz = shape
     F64 = None if F is None else np.asarray(F, dtype=np.float32).astype(np.float64)
     return oracle.run(lattice, nx, ny, nz, tau, bc, steps, lid=lid, F=F64, p0=p0,
                       u0=None if u0 is None else np.ascontiguousarray(u0).ravel(),
-                      compressible=compressible, rho0=rho0)
+                      compressible=compressible, rho0=rho0, trt_lambda=trt_lambda)
 
 
 def errors(gpu, ref, uref, rho0=1.0):
@@ -187,6 +189,88 @@ def test_poiseuille_on_gpu():
     y = np.arange(ny)
     parabola = np.float64(np.float32(G)) / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
     assert np.abs(u[0] - parabola).max() < 1e-9 * parabola.max()
+
+
+# ---------------------------------------------------------------------------
+# Two-relaxation-time collision
+
+
+TRT_CASES = [
+    ("d3q19", (37, 29, 23), "cavity", 3 / 16),
+    ("d3q27", (41, 9, 6), "channel", 1 / 4),
+    ("d2q9", (45, 33, 1), "periodic", 1 / 12),
+    ("d3q19", (300, 7, 5), "channel", 3 / 16),
+]
+
+
+@pytest.mark.parametrize("lattice,shape,bc,lam", TRT_CASES)
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("aa", [False, True])
+def test_trt_parity(lattice, shape, bc, lam, storage, aa):
+    Q, d = oracle.dims(lattice)
+    nx, ny, nz = shape
+    p0, u0 = W.random_smooth_state(nx, ny, nz, d, amp_u=0.04, amp_p=2e-3, seed=23)
+    lid = (0.08, 0.0, 0.02) if bc != "periodic" else None
+    F = W.fourier_force(nx, ny, nz, amplitude=2e-5, seed=7, dims=d)
+    steps = 61
+    ref = oracle_run(lattice, shape, 0.62, bc, steps, lid=lid, F=F, p0=p0, u0=u0,
+                     trt_lambda=lam)
+    got = gpu_run(lattice, shape, 0.62, bc, steps, storage=storage, aa=aa, lid=lid, F=F,
+                  p0=p0, u0=u0, trt_lambda=lam)
+    eu, ep = errors(got, ref, 0.05)
+    assert eu < TOL[storage] and ep < 10 * TOL[storage], (eu, ep)
+    # and it is not BGK: the same run without TRT differs well above rounding
+    if storage == "f64":
+        bgk = oracle_run(lattice, shape, 0.62, bc, steps, lid=lid, F=F, p0=p0, u0=u0)
+        assert errors(got, bgk, 0.05)[0] > 1e3 * TOL["f64"]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_trt_poiseuille_on_gpu(storage):
+    """TRT with Lambda = 3/16 at tau = 1.5: the exact parabola (BGK misses it by 3 %)."""
+    ny, G, tau = 14, 1e-5, 1.5
+    nu = W.viscosity(tau)
+    F = np.zeros((3, ny), dtype=np.float32)
+    F[0] = G
+    _, u, _ = gpu_run("d3q19", (1, ny, 1), tau, "channel", int(30 * ny * ny / nu),
+                      storage=storage, F=F, trt_lambda=3 / 16)
+    y = np.arange(ny)
+    parabola = np.float64(np.float32(G)) / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    tol = 1e-9 if storage == "f64" else 1e-3
+    assert np.abs(u[0] - parabola).max() < tol * parabola.max()
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s", "bf16s"])
+@pytest.mark.parametrize("bc", ["cavity", "channel"])
+def test_trt_aa_equals_pull_bitwise(storage, bc):
+    shape = (45, 26, 19)
+    p0, u0 = W.random_smooth_state(*shape, 3, amp_u=0.04, seed=13)
+    F = W.fourier_force(*shape, amplitude=2e-5, seed=3, dims=3)
+    for steps in (10, 11):
+        a = gpu_run("d3q19", shape, 0.6, bc, steps, storage=storage, aa=False, lid=(0.07, 0, 0),
+                    p0=p0, u0=u0, F=F, trt_lambda=3 / 16)
+        b = gpu_run("d3q19", shape, 0.6, bc, steps, storage=storage, aa=True, lid=(0.07, 0, 0),
+                    p0=p0, u0=u0, F=F, trt_lambda=3 / 16)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), steps
+
+
+@pytest.mark.parametrize("lattice,shape", [("d3q19", (520, 9, 7)), ("d3q27", (264, 7, 6)),
+                                           ("d2q9", (304, 37, 1))])
+@pytest.mark.parametrize("storage", ["f32", "f16s", "bf16s"])
+def test_trt_kernel_variants_bitwise(lattice, shape, storage):
+    """Plain, staged and (16-bit) paired kernels give identical TRT results."""
+    Q, d = oracle.dims(lattice)
+    p0, u0 = W.random_smooth_state(*shape, d, amp_u=0.04, seed=45)
+    F = W.fourier_force(*shape, amplitude=2e-5, seed=9, dims=d)
+    kernels = ["plain", "staged"] + (["paired"] if storage != "f32" else [])
+    for aa, steps in ((False, 9), (True, 9), (True, 10)):
+        outs = [gpu_run(lattice, shape, 0.6, "cavity", steps, storage=storage, aa=aa,
+                        lid=(0.07, 0.0, 0.01), p0=p0, u0=u0, F=F, trt_lambda=3 / 16,
+                        kernel=k) for k in kernels]
+        for k, o in zip(kernels[1:], outs[1:]):
+            assert outs[0][2].kernel == "plain" and o[2].kernel == k
+            assert np.array_equal(outs[0][0], o[0]) and np.array_equal(outs[0][1], o[1]), \
+                (k, aa, steps)
 
 
 # ---------------------------------------------------------------------------

@@ -112,6 +112,52 @@ def test_collision_invariants(lattice):
         assert np.abs(E.T @ outF - (E.T @ f + F)).max() < 1e-15
 
 
+def _moment(E, f, powers):
+    """sum_a e_ax^i e_ay^j e_az^k f_a for powers = (i, j, k)."""
+    m = np.ones(len(f))
+    for k, p in enumerate(powers):
+        if p:
+            m = m * E[:, k] ** p
+    return (m * f).sum()
+
+
+@pytest.mark.parametrize("lattice", LATTICES)
+def test_trt_collision_moments(lattice):
+    """TRT keeps P and j (the force adds F), leaves feq fixed, relaxes the
+    non-equilibrium part of every even moment by (1 - omega) and of every odd
+    moment by (1 - omega_m); Lambda = (tau - 1/2)^2 is BGK."""
+    rng = np.random.default_rng(9)
+    e, t, _ = oracle.tables(lattice)
+    Q, d = oracle.dims(lattice)
+    E = np.zeros((Q, 3))
+    E[:, :d] = e[:, :d]
+    for tau, lam in ((0.55, 3 / 16), (0.8, 1 / 4), (1.7, 1 / 12)):
+        om = 1 / tau
+        om_m = 1 / (lam / (tau - 0.5) + 0.5)
+        f = t * (1 + 0.05 * rng.standard_normal(Q))
+        out = oracle.collide_node(lattice, f, tau, trt_lambda=lam)
+        assert abs(out.sum() - f.sum()) < 1e-15
+        assert np.abs(E.T @ out - E.T @ f).max() < 1e-15
+        feq = oracle.equilibrium(lattice, f.sum(), (E.T @ f)[:d])
+        assert np.abs(oracle.collide_node(lattice, feq, tau, trt_lambda=lam) - feq).max() < 1e-15
+        # moments of the non-equilibrium part (F = 0): parity of the total
+        # power decides the rate
+        for pw in [(1, 1, 0), (2, 0, 0), (0, 2, 0), (1, 2, 0), (2, 1, 0), (2, 2, 0), (3, 0, 0),
+                   (1, 0, 0), (0, 1, 0)] + ([(1, 1, 1), (0, 1, 2), (1, 0, 2)] if d == 3 else []):
+            before = _moment(E, f - feq, pw)
+            after = _moment(E, out - feq, pw)
+            rate = om if sum(pw) % 2 == 0 else om_m
+            assert abs(after - (1 - rate) * before) < 1e-15, (pw, after, before)
+        F = 1e-4 * rng.standard_normal(d)
+        outF = oracle.collide_node(lattice, f, tau, F=F, trt_lambda=lam)
+        assert abs(outF.sum() - f.sum()) < 1e-15
+        assert np.abs(E[:, :d].T @ outF - (E[:, :d].T @ f + F)).max() < 1e-15
+        # BGK as the special case omega_m = omega
+        bgk = oracle.collide_node(lattice, f, tau, F=F)
+        same = oracle.collide_node(lattice, f, tau, F=F, trt_lambda=(tau - 0.5) ** 2)
+        assert np.abs(bgk - same).max() < 1e-15
+
+
 # --------------------------------------------------------------------------
 # Whole scheme: invariants
 
@@ -247,6 +293,41 @@ def test_poiseuille(lattice):
         else:
             assert np.abs(slip).max() < 1e-9 * parabola.max()
         assert np.abs(u[1:]).max() < 1e-10 * parabola.max()
+
+
+@pytest.mark.parametrize("lattice", ["d2q9", "d3q19", "d3q27"])
+def test_trt_poiseuille_exact_for_any_tau(lattice):
+    """With Lambda = 3/16 half-way bounce-back puts the walls exactly half a
+    link out for any tau (Ginzburg's TRT result): the steady body-force channel
+    profile is the parabola to rounding, while BGK at the same tau is not."""
+    ny, G = 12, 1e-5
+    Q, d = oracle.dims(lattice)
+    y = np.arange(ny)
+    for tau in (0.8, 1.5, 3.0):
+        nu = W.viscosity(tau)
+        F = np.zeros((d, ny))
+        F[0] = G
+        steps = int(30 * ny * ny / nu)
+        parabola = G / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+        _, u = oracle.run(lattice, 1, ny, 1, tau, "channel", steps, F=F, trt_lambda=3 / 16)
+        assert np.abs(u[0] - parabola).max() < 1e-10 * parabola.max(), tau
+        assert np.abs(u[1:]).max() < 1e-10 * parabola.max()
+        _, ub = oracle.run(lattice, 1, ny, 1, tau, "channel", steps, F=F)
+        assert np.abs(ub[0] - parabola).max() > 1e-3 * parabola.max(), tau
+
+
+@pytest.mark.parametrize("lam", [1 / 4, 3 / 16, 1 / 12])
+def test_trt_shear_viscosity_set_by_omega(lam):
+    """TRT: the shear-wave decay rate is nu (kx^2 + ky^2) with nu = (tau - 1/2)/3
+    from the even rate alone, whatever Lambda (within 1 %)."""
+    n, tau = 96, 0.8
+    p0, u0 = W.taylor_green_2d(n, n, 0.05)
+    amps = []
+    for T in (100, 900):
+        _, u = oracle.run("d2q9", n, n, 1, tau, "periodic", T, p0=p0, u0=u0, trt_lambda=lam)
+        amps.append(_tg_amplitude(u, n))
+    rate = -math.log(amps[1] / amps[0]) / 800
+    assert abs(rate / W.taylor_green_rate(n, n, tau) - 1) < 0.01
 
 
 @pytest.mark.parametrize("lattice", ["d2q9", "d3q19"])
