@@ -198,18 +198,19 @@ def timed_steps(lat, steps, warmup, world, per_launch=True):
     return total, durs, parity
 
 
-def make_cavity(lattice, n, re, storage, aa, lid_u=0.1):
+def make_cavity(lattice, n, re, storage, aa, lid_u=0.1, trt_lambda=None):
     from paper_2201_11330_b300 import workloads as W
     from paper_2201_11330_b300.lbm import Lattice
     c = W.cavity_params(n, re, lid_u)
-    lat = Lattice(lattice, n, n, n, c["tau"], "cavity", storage=storage, aa=aa, lid=c["lid"])
+    lat = Lattice(lattice, n, n, n, c["tau"], "cavity", storage=storage, aa=aa, lid=c["lid"],
+                  trt_lambda=trt_lambda)
     lat.init()
     return lat
 
 
-def run_cavity(lattice, n, re, storage, aa, steps, warmup, world, device):
+def run_cavity(lattice, n, re, storage, aa, steps, warmup, world, device, trt_lambda=None):
     import torch
-    lat = make_cavity(lattice, n, re, storage, aa)
+    lat = make_cavity(lattice, n, re, storage, aa, trt_lambda=trt_lambda)
     total, durs, parity = timed_steps(lat, steps, warmup, world)
     total = max_over_ranks(total, world, device)
     N = n ** 3
@@ -445,6 +446,11 @@ def main():
                        device)
         r["hbm_frac"] = r["glups"] / world * r["bytes_per_node"] / peak
         extras["d3q19_f32_pull"] = r
+        for st in ("f32", "f16s"):  # two-relaxation-time collision, Lambda = 3/16
+            r = run_cavity("d3q19", hb["n"], hb["re"], st, True, args.steps, args.warmup, world,
+                           device, trt_lambda=3 / 16)
+            r["hbm_frac"] = r["glups"] / world * r["bytes_per_node"] / peak
+            extras[f"d3q19_{st}_aa_trt"] = r
         n27 = 768 if hb["n"] == 512 else hb["n"]
         r = run_cavity("d3q27", n27, 2000.0, "f16s", True, max(10, args.steps // 4),
                        args.warmup, world, device)

@@ -196,10 +196,11 @@ __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coe
         }
     };
     if constexpr (MODEL == M_TRT) {
-        // Two relaxation times: the symmetric half-sum (g_a + g_b)/2 relaxes
-        // at omega towards t sym, the antisymmetric half-difference at
-        // omega_m towards t asym; the source's antisymmetric part carries
-        // (1 - omega_m/2).
+        // Two relaxation times: the even half gp = (g_a + g_b)/2 relaxes at
+        // omega towards t sym, the odd half gm = (g_a - g_b)/2 at omega_m
+        // towards t asym (the source's odd part carries (1 - omega_m/2));
+        // then g_a = gp + gm, g_b = gp - gm.  Built from the pair sums sp, sm
+        // of the moment pass, so g itself is dead by now.
         const R omm = c.omega_m;
         SFor<0, H>::run([&](auto A_) {
             constexpr int a = decltype(A_)::value;
@@ -207,10 +208,11 @@ __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coe
             const R t = R(L::w(a));
             R sym, asym;
             pair_eq(A_, sym, asym);
-            const R hp = o_fma(o_add(g[a], g[b]), R(0.5), -o_mul(sym, t));
-            const R hm = o_fma(o_sub(g[a], g[b]), R(0.5), -o_mul(asym, t));
-            g[a] = o_fma(-omm, hm, o_fma(-om, hp, g[a]));
-            g[b] = o_fma(omm, hm, o_fma(-om, hp, g[b]));
+            const R hp = o_mul(sp[a], R(0.5)), hm = o_mul(sm[a], R(0.5));
+            const R gp = o_fma(om, o_fma(sym, t, -hp), hp);
+            const R gm = o_fma(omm, o_fma(asym, t, -hm), hm);
+            g[a] = o_add(gp, gm);
+            g[b] = o_sub(gp, gm);
         });
     } else {
         SFor<0, H>::run([&](auto A_) {

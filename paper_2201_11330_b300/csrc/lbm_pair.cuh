@@ -160,10 +160,11 @@ __device__ __forceinline__ void collide2(float2 (&g)[L::Q], const float2 (&F)[3]
             const float2 t = v_bc(float(L::w(a)));
             float2 sym, asym;
             pair_eq(A_, sym, asym);
-            const float2 hp = v_fma(v_add(g[a], g[b]), v_bc(0.5f), v_neg(v_mul(sym, t)));
-            const float2 hm = v_fma(v_sub(g[a], g[b]), v_bc(0.5f), v_neg(v_mul(asym, t)));
-            g[a] = v_fma(v_neg(omm), hm, v_fma(v_neg(om), hp, g[a]));
-            g[b] = v_fma(omm, hm, v_fma(v_neg(om), hp, g[b]));
+            const float2 hp = v_mul(sp[a], v_bc(0.5f)), hm = v_mul(sm[a], v_bc(0.5f));
+            const float2 gp = v_fma(om, v_fma(sym, t, v_neg(hp)), hp);
+            const float2 gm = v_fma(omm, v_fma(asym, t, v_neg(hm)), hm);
+            g[a] = v_add(gp, gm);
+            g[b] = v_sub(gp, gm);
         });
     } else {
         SFor<0, H>::run([&](auto A_) {
