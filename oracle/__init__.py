@@ -25,6 +25,9 @@ D2Q9, D3Q19, D3Q27 = 0, 1, 2
 BC_PERIODIC, BC_CAVITY, BC_CHANNEL = 0, 1, 2
 _LATTICE_NAMES = {"d2q9": D2Q9, "d3q19": D3Q19, "d3q27": D3Q27}
 _BC_NAMES = {"periodic": BC_PERIODIC, "cavity": BC_CAVITY, "channel": BC_CHANNEL}
+FACE_PERIODIC, FACE_WALL, FACE_INLET, FACE_OUTFLOW, FACE_SYMMETRY = 0, 1, 2, 3, 4
+_FACE_NAMES = {"periodic": FACE_PERIODIC, "wall": FACE_WALL, "inlet": FACE_INLET,
+               "outflow": FACE_OUTFLOW, "symmetry": FACE_SYMMETRY}
 
 _lib = None
 
@@ -57,8 +60,13 @@ def _load():
         lib.or_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp, dp,
                                    dp, ctypes.c_long, ctypes.c_long, dp, dp, dp, ctypes.c_int]
+        up = ctypes.POINTER(ctypes.c_ubyte)
+        lib.or_run_faces.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_double, ip, ctypes.c_int, ctypes.c_double,
+                                     dp, dp, up, dp, dp, dp, ctypes.c_double, ctypes.c_long,
+                                     dp, dp, dp, dp, ctypes.c_int, ctypes.c_double]
         for f in (lib.or_tables, lib.or_equilibrium, lib.or_collide_node, lib.or_run,
-                  lib.or_adjoint):
+                  lib.or_adjoint, lib.or_run_faces):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -141,14 +149,37 @@ def collide_node(lattice, f, tau, rho0=1.0, compressible=False, F=None, trt_lamb
     return out
 
 
+def faces_of(bc):
+    """Six face types (-x, +x, -y, +y, -z, +z) from names or ints."""
+    out = [(_FACE_NAMES[f] if isinstance(f, str) else int(f)) for f in bc]
+    if len(out) != 6:
+        raise ValueError("six face types expected")
+    return out
+
+
 def run(lattice, nx, ny, nz, tau, bc, steps, *, rho0=1.0, compressible=False, lid=None,
-        F=None, p0=None, u0=None, want_f=False, threads=0, trt_lambda=None):
+        F=None, p0=None, u0=None, want_f=False, threads=0, trt_lambda=None, solid=None,
+        inlet=None, want_force=False, p_outflow=1.0 / 3.0):
     """Forward run of Sec. 3.1's loop for ``steps`` steps.
 
     Returns ``(p, u)`` (or ``(p, u, f)``): p shape (N,), u shape (d, N),
     f shape (Q, N) post-propagation.  ``threads=0`` leaves OpenMP's default.
     ``trt_lambda`` selects the two-relaxation-time collision.
+
+    ``bc`` is "periodic", "cavity", "channel" or a sequence of six face
+    types ("periodic", "wall", "inlet", "outflow", "symmetry"; order -x, +x,
+    -y, +y, -z, +z).  ``solid``: N bytes, nonzero = obstacle node.
+    ``inlet``: inlet velocity, shape (d, face nodes), the face's nodes
+    numbered by its two remaining axes, lower axis fastest.  ``p_outflow``:
+    the pressure p = c_s^2 P held at outflow faces.  With
+    ``want_force`` the momentum-exchange force on the obstacles during the
+    last step (3,) is appended to the result.
     """
+    if not isinstance(bc, str) or solid is not None or inlet is not None or want_force:
+        return _run_faces(lattice, nx, ny, nz, tau, bc, steps, rho0=rho0,
+                          compressible=compressible, lid=lid, F=F, p0=p0, u0=u0, want_f=want_f,
+                          threads=threads, trt_lambda=trt_lambda, solid=solid, inlet=inlet,
+                          want_force=want_force, p_outflow=p_outflow)
     lib = _load()
     Q, d = dims(lattice)
     N = nx * ny * nz
@@ -168,6 +199,47 @@ def run(lattice, nx, ny, nz, tau, bc, steps, *, rho0=1.0, compressible=False, li
     if want_f:
         return p, u, f.reshape(Q, N)
     return p, u
+
+
+def _run_faces(lattice, nx, ny, nz, tau, bc, steps, *, rho0, compressible, lid, F, p0, u0,
+               want_f, threads, trt_lambda, solid, inlet, want_force, p_outflow):
+    lib = _load()
+    Q, d = dims(lattice)
+    N = nx * ny * nz
+    if isinstance(bc, str):
+        named = {"periodic": ["periodic"] * 6, "cavity": ["wall"] * 6,
+                 "channel": ["periodic", "periodic", "wall", "wall", "periodic", "periodic"]}
+        bc = named[bc]
+    faces = (ctypes.c_int * 6)(*faces_of(bc))
+    lid3 = None if lid is None else _f64(np.pad(np.asarray(lid, float), (0, 3 - len(lid))))
+    F = _f64(F, d * N)
+    p0 = _f64(p0, N)
+    u0 = _f64(u0, d * N)
+    sol = None
+    if solid is not None:
+        sol = np.ascontiguousarray(np.asarray(solid).ravel() != 0, dtype=np.uint8)
+        if sol.size != N:
+            raise ValueError("solid needs N values")
+    inl = None if inlet is None else np.ascontiguousarray(np.asarray(inlet, np.float64).ravel())
+    p = np.zeros(N)
+    u = np.zeros(d * N)
+    f = np.zeros(Q * N) if want_f else None
+    force = np.zeros(3) if want_force else None
+    rc = lib.or_run_faces(_lat(lattice), nx, ny, nz, float(tau), faces, int(bool(compressible)),
+                          float(rho0), _dp(lid3), _dp(F),
+                          None if sol is None else sol.ctypes.data_as(
+                              ctypes.POINTER(ctypes.c_ubyte)),
+                          _dp(inl), _dp(p0), _dp(u0), float(p_outflow), int(steps), _dp(p),
+                          _dp(u), _dp(f),
+                          _dp(force), int(threads), float(trt_lambda or 0.0))
+    if rc != 0:
+        raise ValueError(f"or_run_faces failed with status {rc}")
+    out = [p, u.reshape(d, N)]
+    if want_f:
+        out.append(f.reshape(Q, N))
+    if want_force:
+        out.append(force)
+    return tuple(out)
 
 
 def adjoint(lattice, nx, ny, nz, tau, bc, T, K, *, rho0=1.0, lid=None, F=None, p0=None,

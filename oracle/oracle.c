@@ -41,6 +41,26 @@
  *     omega and omega_m, Lambda = (1/omega - 1/2)(1/omega_m - 1/2); the Guo
  *     source splits the same way, its even half scaled by (1 - omega/2), its
  *     odd half by (1 - omega_m/2).  Lambda = 0 selects BGK.
+ *   - per-face boundaries and obstacles (Sec. 4-5 use them; their discrete
+ *     form is not printed): for the population entering fluid node x along
+ *     e_a, take the upstream node x - e_a and fix each coordinate that
+ *     leaves the box by the type of the face it crosses: periodic wraps;
+ *     wall and inlet bounce back half-way (f_a(x) = f*_abar(x) plus
+ *     2 t_a rho0 (e_a . U)/c_s^2 with U the inlet velocity at x for an
+ *     inlet, the lid velocity for the +y wall, else 0; the inlet wins over
+ *     the lid on a link crossing both); outflow is a pressure outlet by
+ *     anti-bounce-back, f_a(x) = -f*_abar(x) + 2 feq+_a(P_out, u(x)) with
+ *     feq+ the even half of the equilibrium and u(x) the node's velocity from
+ *     its post-collision populations (the paper's convective outflow is not
+ *     printed; a velocity inlet needs a pressure level fixed somewhere, and a
+ *     zero-gradient outlet leaves it free to drift); symmetry mirrors the
+ *     coordinate back to that of x and reflects the direction's component
+ *     normal to the face (specular, free slip).  Crossings rank wall/inlet,
+ *     then outflow, then symmetry/periodic.  If the node so found is solid, the
+ *     population bounces back at x as well (stationary obstacle), and the
+ *     link's momentum exchange 2 f*_abar(x) e_abar counts towards the
+ *     force on the obstacle (Sec. 5, momentum exchange of Ladd).  Solid
+ *     nodes are not updated; PostProcessing reports p = 0, u = 0 there.
  *
  * Pins (tests under tests/ check these against closed forms, conservation
  * laws, analytic flows and finite differences): tables, equilibrium moments,
@@ -65,6 +85,9 @@
 
 enum { OR_D2Q9 = 0, OR_D3Q19 = 1, OR_D3Q27 = 2 };
 enum { OR_BC_PERIODIC = 0, OR_BC_CAVITY = 1, OR_BC_CHANNEL = 2 };
+enum { OR_FACE_PERIODIC = 0, OR_FACE_WALL = 1, OR_FACE_INLET = 2, OR_FACE_OUTFLOW = 3,
+       OR_FACE_SYMMETRY = 4 };
+enum { OR_LINK_STREAM = 0, OR_LINK_WALL = 1, OR_LINK_SOLID = 2, OR_LINK_OUTFLOW = 3 };
 enum { OR_OK = 0, OR_ERR_ARG = -1, OR_ERR_NOMEM = -5 };
 
 /* 1/c_s^2 for all three velocity sets (c_s^2 = c^2/3, c = 1). */
@@ -83,6 +106,10 @@ typedef struct {
     long N;
     int periodic[3];
     int lid_on;
+    int face[6];                 /* face types, order -x, +x, -y, +y, -z, +z */
+    const unsigned char *solid;  /* N, nonzero = solid node, or NULL */
+    const double *inlet_u;       /* d * (nodes of the inlet face), or NULL */
+    double P_out;                /* outflow pressure level P = p / c_s^2 */
     double lid[3];
     double omega, rho0;
     double omega_m; /* TRT odd-part rate; 0 = BGK */
@@ -311,10 +338,138 @@ static int upstream(const or_model *m, int x, int y, int z, const int e[3], long
     return 1;
 }
 
-/* BoundaryCondition + Propagation: fb (post-collision) -> f (post-propagation).
- * For every node x and direction a: f_a(x) = fb_a(x - e_a) when the upstream
- * node is in the domain, else the bounce-back f_a(x) = fb_abar(x), plus the
- * moving-wall term when the link crosses the lid. */
+static long node_index(const or_model *m, int x, int y, int z)
+{
+    return (long)x + (long)m->nx * ((long)y + (long)m->ny * z);
+}
+
+static int is_solid(const or_model *m, long n) { return m->solid && m->solid[n]; }
+
+/* Velocity of the inlet face at the face position of node (x, y, z); the
+ * face's nodes are numbered by the two remaining axes, lower axis fastest. */
+static void inlet_velocity(const or_model *m, int x, int y, int z, double U[3])
+{
+    int f = -1;
+    for (int i = 0; i < 6; ++i)
+        if (m->face[i] == OR_FACE_INLET)
+            f = i;
+    long idx, nf;
+    if (f / 2 == 0) {
+        idx = y + (long)m->ny * z;
+        nf = (long)m->ny * m->nz;
+    } else if (f / 2 == 1) {
+        idx = x + (long)m->nx * z;
+        nf = (long)m->nx * m->nz;
+    } else {
+        idx = x + (long)m->nx * y;
+        nf = (long)m->nx * m->ny;
+    }
+    U[0] = U[1] = U[2] = 0.0;
+    for (int k = 0; k < m->v.d; ++k)
+        U[k] = m->inlet_u[k * nf + idx];
+}
+
+/* Where the population entering fluid node (x, y, z) along e_a comes from
+ * (the rule in the header): OR_LINK_STREAM with the source node and slot,
+ * or a bounce (OR_LINK_WALL, OR_LINK_SOLID, OR_LINK_OUTFLOW) involving slot
+ * abar of the node itself, with *term the moving-wall term of a wall or
+ * inlet link. */
+static int resolve_link(const or_model *m, int x, int y, int z, int a, long *src, int *slot,
+                        double *term)
+{
+    const or_dvm *v = &m->v;
+    const int c[3] = {x, y, z}, L[3] = {m->nx, m->ny, m->nz};
+    int up[3], e[3], bounce = 0, inlet = 0, lid = 0, outflow = 0;
+    for (int k = 0; k < 3; ++k) {
+        e[k] = v->e[a][k];
+        up[k] = c[k] - e[k];
+        if (up[k] >= 0 && up[k] < L[k])
+            continue;
+        int face = 2 * k + (up[k] >= L[k] ? 1 : 0);
+        switch (m->face[face]) {
+        case OR_FACE_PERIODIC:
+            up[k] = (up[k] + L[k]) % L[k];
+            break;
+        case OR_FACE_WALL:
+            bounce = 1;
+            if (face == 3)
+                lid = m->lid_on;
+            break;
+        case OR_FACE_INLET:
+            bounce = 1;
+            inlet = 1;
+            break;
+        case OR_FACE_OUTFLOW:
+            outflow = 1;
+            break;
+        case OR_FACE_SYMMETRY:
+            up[k] = c[k];
+            e[k] = -e[k];
+            break;
+        }
+    }
+    *term = 0.0;
+    if (bounce) {
+        double U[3] = {0.0, 0.0, 0.0};
+        if (inlet)
+            inlet_velocity(m, x, y, z, U);
+        else if (lid)
+            for (int k = 0; k < 3; ++k)
+                U[k] = m->lid[k];
+        double eU = v->e[a][0] * U[0] + v->e[a][1] * U[1] + v->e[a][2] * U[2];
+        *term = 2.0 * v->t[a] * m->rho0 * eU * INV_CS2;
+        *src = node_index(m, x, y, z);
+        *slot = v->opp[a];
+        return OR_LINK_WALL;
+    }
+    if (outflow) {
+        *src = node_index(m, x, y, z);
+        *slot = v->opp[a];
+        return OR_LINK_OUTFLOW;
+    }
+    long nu = node_index(m, up[0], up[1], up[2]);
+    if (is_solid(m, nu)) {
+        *src = node_index(m, x, y, z);
+        *slot = v->opp[a];
+        return OR_LINK_SOLID;
+    }
+    /* the (possibly reflected) direction e */
+    int b = -1;
+    for (int i = 0; i < v->Q; ++i)
+        if (v->e[i][0] == e[0] && v->e[i][1] == e[1] && v->e[i][2] == e[2])
+            b = i;
+    *src = nu;
+    *slot = b;
+    return OR_LINK_STREAM;
+}
+
+/* Velocity of node n from its post-collision populations: collision keeps P
+ * and adds F to j, so u = (sum e fb - F/2)/rho. */
+static void post_collision_velocity(const or_model *m, const double *fb, long n, double u[3])
+{
+    const or_dvm *v = &m->v;
+    double s = 0.0, j[3] = {0.0, 0.0, 0.0}, Fn[3];
+    load_force(m, n, Fn);
+    for (int a = 0; a < v->Q; ++a) {
+        s += fb[n * v->Q + a];
+        for (int k = 0; k < 3; ++k)
+            j[k] += v->e[a][k] * fb[n * v->Q + a];
+    }
+    double rho = m->compressible ? s : m->rho0;
+    for (int k = 0; k < 3; ++k)
+        u[k] = (j[k] - 0.5 * Fn[k]) / rho;
+}
+
+/* Even half of the equilibrium, feq+_a(P, u) = (feq_a + feq_abar)/2. */
+static double equilibrium_even(const or_model *m, int a, double P, const double u[3])
+{
+    double feq[OR_MAXQ];
+    equilibrium(&m->v, m->compressible, m->rho0, P, u, feq);
+    return 0.5 * (feq[a] + feq[m->v.opp[a]]);
+}
+
+/* BoundaryCondition + Propagation: fb (post-collision) -> f (post-propagation)
+ * at every fluid node, each population taken where resolve_link says. */
 static void propagate(const or_model *m, const double *fb, double *f)
 {
     const or_dvm *v = &m->v;
@@ -323,21 +478,50 @@ static void propagate(const or_model *m, const double *fb, double *f)
     for (int z = 0; z < m->nz; ++z)
         for (int y = 0; y < m->ny; ++y)
             for (int x = 0; x < m->nx; ++x) {
-                long n = (long)x + (long)m->nx * ((long)y + (long)m->ny * z);
+                long n = node_index(m, x, y, z);
+                if (is_solid(m, n))
+                    continue;
                 for (int a = 0; a < Q; ++a) {
-                    long nu;
-                    int lid;
-                    if (upstream(m, x, y, z, v->e[a], &nu, &lid)) {
-                        f[n * Q + a] = fb[nu * Q + a];
+                    long src;
+                    int slot;
+                    double term;
+                    int kind = resolve_link(m, x, y, z, a, &src, &slot, &term);
+                    if (kind == OR_LINK_OUTFLOW) {
+                        double u[3];
+                        post_collision_velocity(m, fb, n, u);
+                        f[n * Q + a] = -fb[n * Q + v->opp[a]] +
+                                       2.0 * equilibrium_even(m, a, m->P_out, u);
                     } else {
-                        double val = fb[n * Q + v->opp[a]];
-                        if (lid) {
-                            double eU = v->e[a][0] * m->lid[0] + v->e[a][1] * m->lid[1] +
-                                        v->e[a][2] * m->lid[2];
-                            val += 2.0 * v->t[a] * m->rho0 * eU * INV_CS2;
-                        }
-                        f[n * Q + a] = val;
+                        f[n * Q + a] = fb[src * Q + slot] + term;
                     }
+                }
+            }
+}
+
+/* Momentum exchange (Sec. 5): force on the solid nodes during the
+ * propagation fb -> f, sum over fluid nodes x and links a whose source is an
+ * obstacle of 2 fb_abar(x) e_abar (the population leaving x towards the
+ * solid and coming back reversed).  Serial, fixed order. */
+static void obstacle_force(const or_model *m, const double *fb, double out[3])
+{
+    const or_dvm *v = &m->v;
+    const int Q = v->Q;
+    out[0] = out[1] = out[2] = 0.0;
+    for (int z = 0; z < m->nz; ++z)
+        for (int y = 0; y < m->ny; ++y)
+            for (int x = 0; x < m->nx; ++x) {
+                long n = node_index(m, x, y, z);
+                if (is_solid(m, n))
+                    continue;
+                for (int a = 0; a < Q; ++a) {
+                    long src;
+                    int slot;
+                    double term;
+                    if (resolve_link(m, x, y, z, a, &src, &slot, &term) != OR_LINK_SOLID)
+                        continue;
+                    int b = v->opp[a];
+                    for (int k = 0; k < 3; ++k)
+                        out[k] += 2.0 * fb[n * Q + b] * v->e[b][k];
                 }
             }
 }
@@ -347,6 +531,8 @@ static void collide_all(const or_model *m, const double *f, double *fb)
     const int Q = m->v.Q;
 #pragma omp parallel for schedule(static)
     for (long n = 0; n < m->N; ++n) {
+        if (is_solid(m, n))
+            continue;
         double Fn[3];
         load_force(m, n, Fn);
         collide_node(m, f + n * Q, m->F ? Fn : NULL, fb + n * Q);
@@ -362,6 +548,8 @@ static void postprocess(const or_model *m, const double *f, double *p_out, doubl
         double Fn[3], P, u[3];
         load_force(m, n, Fn);
         node_moments(m, f + n * Q, m->F ? Fn : NULL, &P, u);
+        if (is_solid(m, n))
+            P = u[0] = u[1] = u[2] = 0.0;
         if (p_out)
             p_out[n] = P / INV_CS2;
         if (u_out)
@@ -385,9 +573,21 @@ static void init_equilibrium(const or_model *m, const double *p0, const double *
     }
 }
 
-static int setup_model(or_model *m, int lattice, int nx, int ny, int nz, double tau, int bc,
-                       int compressible, double rho0, const double *lid, const double *F,
-                       double trt_lambda)
+/* The three named box types as face types. */
+static int faces_of_bc(int bc, int faces[6])
+{
+    if (bc != OR_BC_PERIODIC && bc != OR_BC_CAVITY && bc != OR_BC_CHANNEL)
+        return OR_ERR_ARG;
+    for (int k = 0; k < 3; ++k) {
+        int periodic = (k == 1) ? (bc == OR_BC_PERIODIC) : (bc != OR_BC_CAVITY);
+        faces[2 * k] = faces[2 * k + 1] = periodic ? OR_FACE_PERIODIC : OR_FACE_WALL;
+    }
+    return OR_OK;
+}
+
+static int setup_model(or_model *m, int lattice, int nx, int ny, int nz, double tau,
+                       const int faces[6], int compressible, double rho0, const double *lid,
+                       const double *F, double trt_lambda)
 {
     memset(m, 0, sizeof(*m));
     if (build_dvm(lattice, &m->v) != OR_OK)
@@ -396,16 +596,26 @@ static int setup_model(or_model *m, int lattice, int nx, int ny, int nz, double 
         return OR_ERR_ARG;
     if (m->v.d == 2 && nz != 1)
         return OR_ERR_ARG;
-    if (bc != OR_BC_PERIODIC && bc != OR_BC_CAVITY && bc != OR_BC_CHANNEL)
+    int ninlet = 0;
+    for (int i = 0; i < 6; ++i) {
+        if (faces[i] < OR_FACE_PERIODIC || faces[i] > OR_FACE_SYMMETRY)
+            return OR_ERR_ARG;
+        /* periodic faces come in pairs */
+        if ((faces[i] == OR_FACE_PERIODIC) != (faces[i ^ 1] == OR_FACE_PERIODIC))
+            return OR_ERR_ARG;
+        /* 2D: no direction leaves through a z face */
+        m->face[i] = (m->v.d == 2 && i >= 4) ? OR_FACE_PERIODIC : faces[i];
+        ninlet += m->face[i] == OR_FACE_INLET;
+    }
+    if (ninlet > 1)
         return OR_ERR_ARG;
     m->nx = nx;
     m->ny = ny;
     m->nz = nz;
     m->N = (long)nx * ny * nz;
-    m->periodic[0] = (bc != OR_BC_CAVITY);
-    m->periodic[1] = (bc == OR_BC_PERIODIC);
-    m->periodic[2] = (bc != OR_BC_CAVITY);
-    m->lid_on = (bc != OR_BC_PERIODIC);
+    for (int k = 0; k < 3; ++k)
+        m->periodic[k] = m->face[2 * k] == OR_FACE_PERIODIC;
+    m->lid_on = m->face[3] == OR_FACE_WALL;
     for (int k = 0; k < 3; ++k)
         m->lid[k] = lid ? lid[k] : 0.0;
     m->omega = 1.0 / tau;
@@ -435,16 +645,26 @@ static void set_threads(int nthreads)
  *   After nsteps steps of Sec. 3.1's loop, writes p (N), u (d*N) and, when
  *   f_out is given, the post-propagation distributions f (Q*N,
  *   direction-major). */
-int or_run(int lattice, int nx, int ny, int nz, double tau, int bc, int compressible,
-           double rho0, const double *lid, const double *F, const double *p0,
-           const double *u0, long nsteps, double *p_out, double *u_out, double *f_out,
-           int nthreads, double trt_lambda)
+int or_run_faces(int lattice, int nx, int ny, int nz, double tau, const int *faces,
+                 int compressible, double rho0, const double *lid, const double *F,
+                 const unsigned char *solid, const double *inlet_u, const double *p0,
+                 const double *u0, double p_outflow, long nsteps, double *p_out,
+                 double *u_out, double *f_out, double *force_out, int nthreads,
+                 double trt_lambda)
 {
     or_model m;
-    int rc = setup_model(&m, lattice, nx, ny, nz, tau, bc, compressible, rho0, lid, F,
+    int rc = setup_model(&m, lattice, nx, ny, nz, tau, faces, compressible, rho0, lid, F,
                          trt_lambda);
     if (rc != OR_OK || nsteps < 0)
         return OR_ERR_ARG;
+    int has_inlet = 0;
+    for (int i = 0; i < 6; ++i)
+        has_inlet |= m.face[i] == OR_FACE_INLET;
+    if (has_inlet && !inlet_u)
+        return OR_ERR_ARG;
+    m.solid = solid;
+    m.inlet_u = inlet_u;
+    m.P_out = p_outflow * INV_CS2;
     set_threads(nthreads);
     const int Q = m.v.Q;
     double *f = malloc(sizeof(double) * Q * m.N);
@@ -455,8 +675,12 @@ int or_run(int lattice, int nx, int ny, int nz, double tau, int bc, int compress
         return OR_ERR_NOMEM;
     }
     init_equilibrium(&m, p0, u0, f);
+    if (force_out)
+        force_out[0] = force_out[1] = force_out[2] = 0.0;
     for (long it = 0; it < nsteps; ++it) {
         collide_all(&m, f, fb);   /* Collision */
+        if (force_out && it == nsteps - 1)
+            obstacle_force(&m, fb, force_out);
         propagate(&m, fb, f);     /* BoundaryCondition + Propagation */
     }
     postprocess(&m, f, p_out, u_out); /* PostProcessing */
@@ -469,13 +693,28 @@ int or_run(int lattice, int nx, int ny, int nz, double tau, int bc, int compress
     return OR_OK;
 }
 
+/* Exported: or_run_faces for the three named box types (no obstacles). */
+int or_run(int lattice, int nx, int ny, int nz, double tau, int bc, int compressible,
+           double rho0, const double *lid, const double *F, const double *p0,
+           const double *u0, long nsteps, double *p_out, double *u_out, double *f_out,
+           int nthreads, double trt_lambda)
+{
+    int faces[6];
+    if (faces_of_bc(bc, faces) != OR_OK)
+        return OR_ERR_ARG;
+    return or_run_faces(lattice, nx, ny, nz, tau, faces, compressible, rho0, lid, F, NULL,
+                        NULL, p0, u0, 1.0 / INV_CS2, nsteps, p_out, u_out, f_out, NULL,
+                        nthreads, trt_lambda);
+}
+
 /* Exported: one collision at one node (tiny brute-force pins). */
 int or_collide_node(int lattice, double tau, int compressible, double rho0, const double *fn,
                     const double *F3, double *out, double trt_lambda)
 {
     or_model m;
-    int rc = setup_model(&m, lattice, 1, 1, 1, tau, OR_BC_PERIODIC, compressible, rho0, NULL,
-                         NULL, trt_lambda);
+    int faces[6] = {0, 0, 0, 0, 0, 0};
+    int rc = setup_model(&m, lattice, 1, 1, 1, tau, faces, compressible, rho0, NULL, NULL,
+                         trt_lambda);
     if (rc != OR_OK)
         return rc;
     collide_node(&m, fn, F3, out);
@@ -611,7 +850,10 @@ int or_adjoint(int lattice, int nx, int ny, int nz, double tau, int bc, double r
                long T, long K, double *J_out, double *dJdF, double *dJdU, int nthreads)
 {
     or_model m;
-    int rc = setup_model(&m, lattice, nx, ny, nz, tau, bc, 0, rho0, lid, F, 0.0);
+    int faces[6];
+    if (faces_of_bc(bc, faces) != OR_OK)
+        return OR_ERR_ARG;
+    int rc = setup_model(&m, lattice, nx, ny, nz, tau, faces, 0, rho0, lid, F, 0.0);
     if (rc != OR_OK || T < 1 || K < 1)
         return OR_ERR_ARG;
     set_threads(nthreads);

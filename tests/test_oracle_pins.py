@@ -392,3 +392,151 @@ def test_adjoint_checkpoint_interval_invariance():
         assert got[0] == ref[0]
         assert np.array_equal(got[1], ref[1])
         assert np.array_equal(got[2], ref[2])
+
+
+# --------------------------------------------------------------------------
+# Per-face boundaries and obstacles (Sec. 4-5 workloads)
+
+CHANNEL_FACES = ["periodic", "periodic", "wall", "wall", "periodic", "periodic"]
+
+
+@pytest.mark.parametrize("lattice", ["d3q19", "d3q27"])
+def test_symmetry_face_equals_mirrored_domain(lattice):
+    """A free-slip symmetry face half a link above the last row gives exactly
+    the lower half of the flow on the doubled, mirror-symmetric domain."""
+    nx, m, nz = 9, 6, 5
+    ny = 2 * m
+    p0h, u0h = W.random_smooth_state(nx, m, nz, 3, amp_u=0.04, seed=3)
+    p0h = p0h.reshape(nz, m, nx)
+    u0h = u0h.reshape(3, nz, m, nx)
+    p0 = np.concatenate([p0h, p0h[:, ::-1]], axis=1).ravel()
+    u0 = np.concatenate([u0h, u0h[:, :, ::-1]], axis=2)
+    u0[1, :, m:] *= -1
+    F = np.zeros((3, nz, ny, nx))
+    F[0] = 1e-5
+    F[2] = -4e-6
+    pf, uf = oracle.run(lattice, nx, ny, nz, 0.7, CHANNEL_FACES, 30, p0=p0,
+                        u0=u0.reshape(3, -1), F=F.reshape(3, -1))
+    half = ["periodic", "periodic", "wall", "symmetry", "periodic", "periodic"]
+    ph, uh = oracle.run(lattice, nx, m, nz, 0.7, half, 30, p0=p0h.ravel(),
+                        u0=u0h.reshape(3, -1), F=np.ascontiguousarray(F[:, :, :m]).reshape(3, -1))
+    assert np.abs(uf.reshape(3, nz, ny, nx)[:, :, :m].reshape(3, -1) - uh).max() < 1e-15
+    assert np.abs(pf.reshape(nz, ny, nx)[:, :m].ravel() - ph).max() < 1e-15
+
+
+def test_solid_rows_equal_walls():
+    """Rows of solid nodes bounce exactly like the walled faces of a channel."""
+    nx, ny, nz = 7, 8, 5
+    p0, u0 = W.random_smooth_state(nx, ny, nz, 3, amp_u=0.04, seed=4)
+    F = W.fourier_force(nx, ny, nz, amplitude=1e-5, seed=2, dims=3)
+    _, uw = oracle.run("d3q19", nx, ny, nz, 0.7, "channel", 25, p0=p0, u0=u0, F=F)
+    P = np.full((nz, ny + 2, nx), 1 / 3)
+    P[:, 1:-1] = p0.reshape(nz, ny, nx)
+    U = np.zeros((3, nz, ny + 2, nx))
+    U[:, :, 1:-1] = u0.reshape(3, nz, ny, nx)
+    Fs = np.zeros((3, nz, ny + 2, nx))
+    Fs[:, :, 1:-1] = F.reshape(3, nz, ny, nx)
+    sol = np.zeros((nz, ny + 2, nx), np.uint8)
+    sol[:, 0] = sol[:, -1] = 1
+    ps, us = oracle.run("d3q19", nx, ny + 2, nz, 0.7, "periodic", 25, p0=P.ravel(),
+                        u0=U.reshape(3, -1), F=Fs.reshape(3, -1), solid=sol)
+    assert np.abs(us.reshape(3, nz, ny + 2, nx)[:, :, 1:-1].reshape(3, -1) - uw).max() < 1e-16
+    # solid nodes report zero
+    assert np.all(ps.reshape(nz, ny + 2, nx)[:, 0] == 0) and np.all(us[:, sol.ravel() != 0] == 0)
+
+
+@pytest.mark.parametrize("lattice", ["d2q9", "d3q19", "d3q27"])
+def test_obstacle_force_balances_momentum(lattice):
+    """Momentum-exchange force: per step, the change of the fluid's total
+    momentum equals the body force on the fluid minus the force on the
+    obstacle (exactly, periodic box, stationary obstacle)."""
+    Q, d = oracle.dims(lattice)
+    nx, ny, nz = (16, 12, 1) if d == 2 else (12, 10, 8)
+    sol = np.zeros((nz, ny, nx), np.uint8)
+    if d == 2:
+        sol[0, 4:7, 5:9] = 1
+    else:
+        sol[3:5, 4:7, 5:8] = 1
+    fl = sol.ravel() == 0
+    Fb = np.zeros((d, nx * ny * nz))
+    Fb[0] = 1e-5
+    Fb[1] = 3e-6
+    p0, u0 = W.random_smooth_state(nx, ny, nz, d, amp_u=0.02, seed=5)
+    u0[:, ~fl] = 0
+    mom = []
+    for k in (10, 11):
+        _, u, Fo = oracle.run(lattice, nx, ny, nz, 0.8, "periodic", k, p0=p0, u0=u0, F=Fb,
+                              solid=sol, want_force=True)
+        mom.append(u[:, fl].sum(axis=1))
+    change = mom[1] - mom[0]
+    assert np.abs(change - (Fb[:, fl].sum(axis=1) - Fo[:d])).max() < 1e-14
+    assert np.abs(Fo[:d]).max() > 1e-3  # the obstacle does take a force
+
+
+@pytest.mark.parametrize("lattice", ["d2q9", "d3q19", "d3q27"])
+def test_uniform_flow_through_open_faces_is_steady(lattice):
+    """A uniform flow entering through a velocity inlet, leaving through a
+    zero-gradient outflow, between free-slip planes, is an exact fixed point."""
+    Q, d = oracle.dims(lattice)
+    nx, ny, nz = (10, 6, 1) if d == 2 else (10, 6, 4)
+    U0 = 0.05
+    u0 = np.zeros((d, nx * ny * nz))
+    u0[0] = U0
+    inl = np.zeros((d, ny * nz))
+    inl[0] = U0
+    faces = ["inlet", "outflow", "symmetry", "symmetry", "periodic", "periodic"]
+    p, u = oracle.run(lattice, nx, ny, nz, 0.7, faces, 20, u0=u0, inlet=inl)
+    assert np.abs(u - u0).max() < 1e-15 and np.abs(p - 1 / 3).max() < 1e-15
+    # a wrong inlet speed is not steady
+    _, u = oracle.run(lattice, nx, ny, nz, 0.7, faces, 20, u0=u0, inlet=1.1 * inl)
+    assert np.abs(u - u0).max() > 1e-4
+
+
+def test_open_faces_are_axis_permutation_invariant():
+    """The same inlet/outflow/wall/symmetry channel set up along x and along y
+    (axes swapped, inlet profile re-indexed) gives the swapped fields."""
+    nx, ny, nz = 14, 9, 6
+    y, z = np.meshgrid(np.arange(ny), np.arange(nz), indexing="xy")
+    prof = 0.04 * (y + 0.5) * (ny - 0.5 - y) / (ny / 2) ** 2 * (1 + 0.1 * np.sin(2 * np.pi * z / nz))
+    inl = np.zeros((3, ny * nz))
+    inl[0] = prof.ravel()
+    fa = ["inlet", "outflow", "wall", "wall", "symmetry", "symmetry"]
+    _, ua = oracle.run("d3q19", nx, ny, nz, 0.7, fa, 40, inlet=inl)
+    # swapped: box (ny, nx, nz), inlet on -y, face nodes numbered (x, z)
+    inl_b = np.zeros((3, ny * nz))
+    inl_b[1] = prof.ravel()  # (x fastest, then z): x of b is y of a
+    fb = ["wall", "wall", "inlet", "outflow", "symmetry", "symmetry"]
+    _, ub = oracle.run("d3q19", ny, nx, nz, 0.7, fb, 40, inlet=inl_b)
+    ua4 = ua.reshape(3, nz, ny, nx)
+    ub4 = ub.reshape(3, nz, nx, ny)
+    assert np.abs(ua4[0] - ub4[1].transpose(0, 2, 1)).max() < 1e-15
+    assert np.abs(ua4[1] - ub4[0].transpose(0, 2, 1)).max() < 1e-15
+    assert np.abs(ua4[2] - ub4[2].transpose(0, 2, 1)).max() < 1e-15
+    assert np.abs(ua4[0]).max() > 0.01
+
+
+def test_inflow_outflow_channel_develops_poiseuille():
+    """Parabolic velocity inlet, pressure outlet, no-slip walls: the flux is
+    the inlet's at every section, the mid-channel profile is the inlet
+    parabola (within 1 %) and the pressure gradient is Poiseuille's,
+    -dp/dx = 8 rho0 nu u_max / H^2 (within 2 %); the outlet holds p_out."""
+    nx, ny, tau = 120, 16, 0.8
+    nu = W.viscosity(tau)
+    y = np.arange(ny)
+    umax = 0.05
+    prof = umax * (y + 0.5) * (ny - 0.5 - y) / (ny / 2) ** 2
+    inl = np.zeros((2, ny))
+    inl[0] = prof
+    u0 = np.zeros((2, nx * ny))
+    u0[0] = np.tile(prof[:, None], (1, nx)).ravel()
+    faces = ["inlet", "outflow", "wall", "wall", "periodic", "periodic"]
+    p, u = oracle.run("d2q9", nx, ny, 1, tau, faces, 8000, u0=u0, inlet=inl, p_outflow=0.33)
+    U = u.reshape(2, ny, nx)
+    P = p.reshape(ny, nx)
+    flux = U[0].sum(axis=0)
+    assert np.abs(flux / prof.sum() - 1).max() < 1e-4
+    assert np.abs(U[0, :, nx // 2] - prof).max() < 0.01 * umax
+    assert np.abs(U[1, :, nx // 2]).max() < 1e-3 * umax
+    slope = (P[:, 40] - P[:, 80]).mean() / 40
+    assert abs(slope / (8 * nu * umax / ny ** 2) - 1) < 0.02
+    assert abs(P[:, -1].mean() - 0.33) < 0.01 * (P[:, 0].mean() - 0.33)
