@@ -62,7 +62,44 @@ typedef enum {
 
 typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 } lbm_lattice;
 
-typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_CAVITY = 1, LBM_BC_CHANNEL = 2 } lbm_bc;
+/* Box types.  LBM_BC_FACES takes one lbm_face per face from lbm_opts.faces. */
+typedef enum {
+    LBM_BC_PERIODIC = 0,
+    LBM_BC_CAVITY = 1,
+    LBM_BC_CHANNEL = 2,
+    LBM_BC_FACES = 3
+} lbm_bc;
+
+/* Per-face boundary conditions (the workloads of Sec. 4-5: channel flow past
+ * a cylinder with a parabolic inlet and an outflow, flow past a sphere with
+ * symmetry planes).  For the population entering node x along e_a the
+ * upstream node x - e_a is fixed, coordinate by coordinate, by the face each
+ * coordinate leaves through:
+ *   LBM_FACE_PERIODIC  wraps (both faces of an axis must be periodic);
+ *   LBM_FACE_WALL      half-way bounce-back, f_a(x) = f*_abar(x); the +y wall
+ *                      adds the lid term 2 t_a rho0 (e_a . U)/c_s^2;
+ *   LBM_FACE_INLET     half-way bounce-back with the term of the inlet
+ *                      velocity (lbm_set_inlet) at x; at most one inlet face;
+ *   LBM_FACE_OUTFLOW   pressure outlet by anti-bounce-back,
+ *                      f_a(x) = -f*_abar(x) + 2 feq+_a(P_out, u(x)), feq+ the
+ *                      even half of the equilibrium at P_out =
+ *                      opts.p_outflow / c_s^2, u(x) the node's velocity from
+ *                      its post-collision populations (the paper names a
+ *                      convective outflow without printing it; behind a
+ *                      velocity inlet an outlet must fix the pressure level);
+ *   LBM_FACE_SYMMETRY  specular reflection (free slip): the coordinate stays
+ *                      that of x and the direction's normal component flips.
+ * A link crossing a wall or inlet bounces whatever else it crosses; then
+ * outflow wins over symmetry and periodic.  The inlet term wins over the lid
+ * term on a link crossing both.  Faces are ordered -x, +x, -y, +y, -z, +z;
+ * D2Q9 ignores the z faces. */
+typedef enum {
+    LBM_FACE_PERIODIC = 0,
+    LBM_FACE_WALL = 1,
+    LBM_FACE_INLET = 2,
+    LBM_FACE_OUTFLOW = 3,
+    LBM_FACE_SYMMETRY = 4
+} lbm_face;
 
 /* Storage of the distributions in HBM.  Arithmetic is FP64 for LBM_F64 and
  * FP32 otherwise.  The "shifted" forms store f_a - t_a (t_a the lattice
@@ -94,12 +131,16 @@ typedef struct {
     int has_force;      /* 1: a body-force field will be set with lbm_set_force */
     int collision;      /* lbm_collision (default BGK) */
     double trt_lambda;  /* TRT magic parameter (> 0), e.g. 3/16 */
+    int faces[6];       /* lbm_face per face (-x, +x, -y, +y, -z, +z), LBM_BC_FACES only */
+    int geometry;       /* 1: solid obstacles will be set with lbm_set_geometry */
+    double p_outflow;   /* pressure held at outflow faces (> 0, default 1/3) */
 } lbm_opts;
 
 typedef struct lbm_ctx lbm_ctx;
 
 /* Defaults: LBM_F32, pull scheme, incompressible, BGK, shifted, rho0 = 1,
- * lid 0, trt_lambda 3/16 (used only with LBM_COLL_TRT). */
+ * lid 0, trt_lambda 3/16 (used only with LBM_COLL_TRT), all faces periodic
+ * (used only with LBM_BC_FACES), no obstacles, p_outflow 1/3. */
 void lbm_default_opts(lbm_opts *opts);
 
 /* tau_std = tau_paper + 1/2 (Sec. 3.3: "ome = 1/(tau+0.5)"). */
@@ -114,8 +155,11 @@ size_t lbm_workspace_bytes(int lattice, int nx, int ny, int nz, const lbm_opts *
  * the case is fixed here.  dev_workspace: caller-owned device memory of
  * `bytes` >= lbm_workspace_bytes(); cuda_stream: cudaStream_t or NULL.
  * Errors: LBM_ERR_ARG (bad lattice/bc/storage, sizes < 1, nz != 1 for D2Q9,
- * tau <= 1/2, rho0 <= 0, N >= 2^31, misaligned workspace), LBM_ERR_NOMEM
- * (workspace too small). */
+ * tau <= 1/2, rho0 <= 0, N >= 2^31, misaligned workspace; with LBM_BC_FACES
+ * or opts.geometry: an unpaired periodic face, more than one inlet, or the
+ * AA scheme, which supports the three named box types only), LBM_ERR_NOMEM
+ * (workspace too small).  LBM_BC_FACES and obstacles run the general step
+ * kernel (pull scheme, one node per thread). */
 int lbm_create(int lattice, int nx, int ny, int nz, double tau, int bc, const lbm_opts *opts,
                void *dev_workspace, size_t bytes, void *cuda_stream, lbm_ctx **out);
 
@@ -136,6 +180,33 @@ int lbm_set_force(lbm_ctx *ctx, const float *force);
 
 /* Moving-wall velocity U (3 values, host).  Takes effect at the next step. */
 int lbm_set_lid(lbm_ctx *ctx, const double *lid_u3);
+
+/* Solid obstacles (Sec. 4-5 geometries; the paper's geo mask): solid is a
+ * device array of N bytes, nonzero = solid node.  Requires opts.geometry = 1
+ * at creation (LBM_ERR_STATE otherwise).  Builds one 32-bit link word per
+ * node in the workspace (which of the node's incoming links start on a
+ * solid node) and counts the fluid nodes; the mask itself is not kept.
+ * Solid nodes are never updated, lbm_macroscopic reports p = 0 and u = 0
+ * there, and lbm_reduce / lbm_step_reduce sum over fluid nodes only.
+ * Invalidates the state: call lbm_init (or lbm_set_state) afterwards.
+ * Synchronises the stream. */
+int lbm_set_geometry(lbm_ctx *ctx, const uint8_t *solid);
+
+/* Inlet velocity of the LBM_FACE_INLET face: device FP32, d * (face nodes)
+ * values, component-major, the face's nodes numbered by its two remaining
+ * axes with the lower axis fastest (face -x/+x: y + ny*z; -y/+y: x + nx*z;
+ * -z/+z: x + nx*y).  Borrowed until replaced; NULL (the initial state) is an
+ * inlet at rest.  LBM_ERR_STATE without an inlet face. */
+int lbm_set_inlet(lbm_ctx *ctx, const float *u_in);
+
+/* lbm_step(n), n >= 1, whose last step also sums the momentum exchange on
+ * the solid nodes (Sec. 5, Ladd): over fluid nodes x and links whose source
+ * is solid, 2 f*_abar(x) e_abar, the population that leaves x towards the
+ * obstacle and comes back reversed.  out: host, 3 doubles (force on the
+ * obstacles during that step, lattice units; z = 0 in 2D).  Per-block sums
+ * in the kernel's arithmetic, then FP64 in a fixed order.  Requires
+ * obstacles (LBM_ERR_STATE otherwise).  Synchronises the stream. */
+int lbm_step_force(lbm_ctx *ctx, int64_t n, double *out);
 
 /* Advance n >= 0 time steps (Sec. 3.1 main loop body), one fused kernel
  * launch per step. */
@@ -239,7 +310,8 @@ int lbm_adjoint(lbm_ctx *ctx, int64_t T, int64_t K, void *adj_workspace, size_t 
  * before any stream capture.
  *
  * Arguments: lattice, nx, ny, nz, bc and *opts as given to lbm_create for
- * the context that produced the buffer; state: device buffer of
+ * the context that produced the buffer (one of the three named box types,
+ * no obstacles; LBM_ERR_ARG otherwise); state: device buffer of
  * lbm_state_bytes() bytes in that context's layout; step: the step count
  * lbm_get_state reported (it selects the AA layout); force: the device FP32
  * force field (d*N) the context used, or NULL; cuda_stream: stream to run

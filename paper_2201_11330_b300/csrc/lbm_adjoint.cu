@@ -35,7 +35,7 @@ struct AdjLayout {
 
 bool adj_supported(const lbm_ctx *c)
 {
-    return !c->opts.aa && !c->opts.compressible && c->opts.collision == LBM_COLL_BGK;
+    return !c->opts.aa && !c->opts.compressible && c->opts.collision == LBM_COLL_BGK && !c->geo;
 }
 
 AdjLayout adj_layout(const lbm_ctx *c, int64_t T, int64_t K)

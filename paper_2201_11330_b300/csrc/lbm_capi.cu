@@ -10,6 +10,7 @@
 #include "lbm.h"
 #include "lbm_bulk.cuh"
 #include "lbm_capi_internal.h"
+#include "lbm_geo.cuh"
 #include "lbm_pair.cuh"
 #include "lbm_kernels.cuh"
 
@@ -55,14 +56,47 @@ bool valid_opts(const lbm_opts &o)
         return false;
     if (!(o.rho0 > 0.0) || !isfinite(o.rho0))
         return false;
+    if (o.geometry != 0 && o.geometry != 1)
+        return false;
+    if (!(o.p_outflow > 0.0) || !isfinite(o.p_outflow))
+        return false;
     for (int k = 0; k < 3; ++k)
         if (!isfinite(o.lid_u[k]))
             return false;
     return true;
 }
 
+// Face types of a box: the named types, or opts.faces for LBM_BC_FACES
+// (validated: known types, periodic faces in pairs, at most one inlet; D2Q9
+// z faces periodic).
+bool resolve_faces(int lattice, int bc, const lbm_opts &o, int face[6])
+{
+    if (bc == LBM_BC_FACES) {
+        for (int i = 0; i < 6; ++i)
+            face[i] = o.faces[i];
+    } else if (bc >= LBM_BC_PERIODIC && bc <= LBM_BC_CHANNEL) {
+        for (int k = 0; k < 3; ++k) {
+            const bool periodic = k == 1 ? bc == LBM_BC_PERIODIC : bc != LBM_BC_CAVITY;
+            face[2 * k] = face[2 * k + 1] = periodic ? LBM_FACE_PERIODIC : LBM_FACE_WALL;
+        }
+    } else {
+        return false;
+    }
+    if (lattice == LBM_D2Q9)
+        face[4] = face[5] = LBM_FACE_PERIODIC;
+    int ninlet = 0;
+    for (int i = 0; i < 6; ++i) {
+        if (face[i] < LBM_FACE_PERIODIC || face[i] > LBM_FACE_SYMMETRY)
+            return false;
+        if ((face[i] == LBM_FACE_PERIODIC) != (face[i ^ 1] == LBM_FACE_PERIODIC))
+            return false;
+        ninlet += face[i] == LBM_FACE_INLET;
+    }
+    return ninlet <= 1;
+}
+
 struct Layout {
-    size_t state_bytes, f_off[2], partial_off, result_off, step_partial_off, total;
+    size_t state_bytes, f_off[2], partial_off, result_off, step_partial_off, links_off, total;
     int nred;
     long long step_blocks;
 };
@@ -90,6 +124,9 @@ Layout layout_for(int lattice, int nx, int ny, int nz, const lbm_opts &o)
     L.step_blocks = nseg;
     L.step_partial_off = off;
     off += align_up((size_t)L.step_blocks * kPartialStride * sizeof(double));
+    L.links_off = off;
+    if (o.geometry)
+        off += align_up(N * sizeof(unsigned));
     L.total = off;
     return L;
 }
@@ -126,7 +163,14 @@ void fill_params(lbm_ctx *c)
     p.nz = c->nz;
     p.N = (int)c->N;
     p.periodic = c->bc == LBM_BC_PERIODIC ? 7 : c->bc == LBM_BC_CHANNEL ? 5 : 0;
-    p.lid_on = c->bc != LBM_BC_PERIODIC;
+    p.lid_on = c->face[3] == LBM_FACE_WALL;
+    p.inlet_face = -1;
+    for (int i = 0; i < 6; ++i) {
+        p.face[i] = c->face[i];
+        if (c->face[i] == LBM_FACE_INLET)
+            p.inlet_face = i;
+    }
+    p.links = c->links_ready ? c->links : nullptr;
     const double omega = 1.0 / c->tau;
     const double sigma = c->shifted ? 1.0 : 0.0;
     // TRT: Lambda = (1/omega - 1/2)(1/omega_m - 1/2); BGK: omega_m = omega
@@ -146,6 +190,12 @@ void fill_params(lbm_ctx *c)
     p.cf.inv_rho0 = (float)(1.0 / c->opts.rho0);
     p.cf.sigma = (float)sigma;
     p.cf.kf = (float)p.cd.kf;
+    // pressure outlet: 2 feq+ - 2 sigma t = t [2 (P_out - sigma)] + 2 t r (...)
+    const double P_out = c->opts.p_outflow * 3.0;
+    p.cd.pout2 = 2.0 * (P_out - sigma);
+    p.cd.pout_r = c->opts.compressible ? P_out : c->opts.rho0;
+    p.cf.pout2 = (float)p.cd.pout2;
+    p.cf.pout_r = (float)p.cd.pout_r;
     for (int a = 0; a < kMaxQ; ++a) {
         p.cd.lid[a] = 0.0;
         p.cf.lid[a] = 0.0f;
@@ -159,6 +209,9 @@ void fill_params(lbm_ctx *c)
     p.F = c->force;
     p.u_out = nullptr;
 }
+
+// p.inlet survives fill_params (which lbm_set_lid calls)
+void keep_inlet(lbm_ctx *c, const float *inlet) { c->sp.inlet = inlet; }
 
 // The staged kernel copies whole 16-byte aligned row segments: nx (hence N)
 // must be a multiple of 16 bytes' worth of values.
@@ -220,7 +273,7 @@ Launch ctx_base_launch(const lbm_ctx *c, int kind) { return base_launch(c, kind)
 cudaError_t ctx_dispatch(const lbm_ctx *c, const Launch &l) { return dispatch(c->lattice, l); }
 
 int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u_out,
-                    long long *reduce_blocks)
+                    long long *reduce_blocks, bool obstacle_force)
 {
     Launch l = base_launch(c, K_STEP);
     l.pattern = pattern;
@@ -228,6 +281,14 @@ int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u
     l.dst = dst;
     if (reduce_blocks)
         l.sp.partials = c->step_partials;
+    if (c->geo) {
+        // the general kernel: pull scheme, one node per thread
+        l.geo = true;
+        l.mon = reduce_blocks ? (obstacle_force ? 2 : 1) : 0;
+        if (reduce_blocks)
+            *reduce_blocks = (long long)l.grid.x * l.grid.y * l.grid.z;
+        return dispatch(c->lattice, l) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+    }
     if (u_out) {
         l.uout = true;
         l.sp.u_out = u_out;
@@ -267,6 +328,7 @@ int ctx_launch_moments(lbm_ctx *c, const void *src, int form, void *p_out, void 
     l.mp.partials = partials;
     l.mp.xseg = (c->nx + c->bx - 1) / c->bx;
     l.mp.nseg = l.mp.xseg * c->ny * c->nz;
+    l.mp.links = c->sp.links;
     l.grid = dim3(c->nred, 1, 1);
     return dispatch(c->lattice, l) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
@@ -294,6 +356,7 @@ void lbm_default_opts(lbm_opts *o)
     o->rho0 = 1.0;
     o->collision = LBM_COLL_BGK;
     o->trt_lambda = 3.0 / 16.0;
+    o->p_outflow = 1.0 / 3.0;
 }
 
 double lbm_tau_from_paper(double tau_paper) { return tau_paper + 0.5; }
@@ -325,7 +388,11 @@ int lbm_create(int lattice, int nx, int ny, int nz, double tau, int bc, const lb
         return LBM_ERR_ARG;
     if (!(tau > 0.5) || !isfinite(tau))
         return LBM_ERR_ARG;
-    if (bc < LBM_BC_PERIODIC || bc > LBM_BC_CHANNEL)
+    int face[6];
+    if (!resolve_faces(lattice, bc, o, face))
+        return LBM_ERR_ARG;
+    const bool geo = bc == LBM_BC_FACES || o.geometry;
+    if (geo && o.aa)
         return LBM_ERR_ARG;
     if (!dev_workspace || ((uintptr_t)dev_workspace % kAlign) != 0)
         return LBM_ERR_ARG;
@@ -369,7 +436,15 @@ int lbm_create(int lattice, int nx, int ny, int nz, double tau, int bc, const lb
     c->kernel_variant = LBM_KERNEL_AUTO;
     c->num_sms = 0;
     c->err = (unsigned *)((char *)c->result + 64);
+    c->geo = geo;
+    for (int i = 0; i < 6; ++i)
+        c->face[i] = face[i];
+    c->links = o.geometry ? (unsigned *)(c->ws + L.links_off) : nullptr;
+    c->links_ready = false;
+    c->count = (unsigned long long *)((char *)c->result + 128);
+    c->n_fluid = c->N;
     fill_params(c);
+    c->sp.inlet = nullptr;
     *out = c;
     return LBM_OK;
 }
@@ -423,7 +498,47 @@ int lbm_set_lid(lbm_ctx *c, const double *lid_u3)
         return LBM_OK;
     for (int k = 0; k < 3; ++k)
         c->opts.lid_u[k] = lid_u3[k];
+    const float *inlet = c->sp.inlet;
     fill_params(c);
+    keep_inlet(c, inlet);
+    return LBM_OK;
+}
+
+int lbm_set_geometry(lbm_ctx *c, const uint8_t *solid)
+{
+    if (!c || !solid)
+        return LBM_ERR_ARG;
+    if (!c->opts.geometry)
+        return LBM_ERR_STATE;
+    if (cudaMemsetAsync(c->count, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    Launch l = base_launch(c, K_LINKS);
+    l.storage = LBM_F32;  // the link kernel is instantiated once per lattice
+    l.solid = solid;
+    l.links = c->links;
+    l.nsolid = c->count;
+    if (dispatch(c->lattice, l) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    unsigned long long nsolid = 0;
+    if (cudaMemcpyAsync(&nsolid, c->count, sizeof(nsolid), cudaMemcpyDeviceToHost, c->stream) !=
+        cudaSuccess)
+        return LBM_ERR_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    c->n_fluid = c->N - (int64_t)nsolid;
+    c->links_ready = true;
+    c->sp.links = c->links;
+    c->initialized = false;
+    return LBM_OK;
+}
+
+int lbm_set_inlet(lbm_ctx *c, const float *u_in)
+{
+    if (!c)
+        return LBM_ERR_ARG;
+    if (c->sp.inlet_face < 0)
+        return LBM_ERR_STATE;
+    keep_inlet(c, u_in);
     return LBM_OK;
 }
 
@@ -460,6 +575,8 @@ int lbm_set_kernel_variant(lbm_ctx *c, int variant)
         return LBM_ERR_ARG;
     if (variant == LBM_KERNEL_PAIRED && !pair_eligible(c))
         return LBM_ERR_ARG;
+    if (c->geo && variant != LBM_KERNEL_AUTO && variant != LBM_KERNEL_PLAIN)
+        return LBM_ERR_ARG;
     c->kernel_variant = variant;
     return LBM_OK;
 }
@@ -468,6 +585,8 @@ int lbm_kernel_variant_in_use(const lbm_ctx *c)
 {
     if (!c)
         return LBM_ERR_ARG;
+    if (c->geo)
+        return LBM_KERNEL_PLAIN;
     return use_pair(c) ? LBM_KERNEL_PAIRED : use_bulk(c) ? LBM_KERNEL_STAGED : LBM_KERNEL_PLAIN;
 }
 
@@ -506,13 +625,48 @@ int lbm_step_reduce(lbm_ctx *c, int64_t n, double *out)
     memcpy(&errword, (const char *)r + 64, sizeof(errword));
     if (errword != 0)
         return LBM_ERR_CUDA;
-    out[0] = r[0] + (c->shifted ? (double)c->N : 0.0);
+    out[0] = r[0] + (c->shifted ? (double)c->n_fluid : 0.0);
     for (int k = 1; k < 5; ++k)
         out[k] = r[k];
     out[5] = sqrt(r[5]);
     for (int k = 0; k < kReduceVals; ++k)
         if (!isfinite(out[k]))
             return LBM_ERR_UNSTABLE;
+    return LBM_OK;
+}
+
+int lbm_step_force(lbm_ctx *c, int64_t n, double *out)
+{
+    if (!c || n < 1 || !out)
+        return LBM_ERR_ARG;
+    if (!c->initialized)
+        return LBM_ERR_STATE;
+    if (!c->links_ready)
+        return LBM_ERR_STATE;
+    int rc = lbm_step(c, n - 1);
+    if (rc != LBM_OK)
+        return rc;
+    long long nb = 0;
+    rc = ctx_launch_step(c, c->f[c->cur], c->f[1 - c->cur], PAT_PULL, nullptr, &nb, true);
+    if (rc != LBM_OK)
+        return rc;
+    c->cur = 1 - c->cur;
+    ++c->step;
+    const int nout = (int)(nb < c->nred ? nb : c->nred);
+    if (launch_chunks(c->step_partials, nb, c->partials, nout, c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    if (launch_finish(c->partials, nout, c->result, c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    double r[3];
+    if (cudaMemcpyAsync(r, c->result, sizeof(r), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    for (int k = 0; k < 3; ++k) {
+        out[k] = r[k];
+        if (!isfinite(out[k]))
+            return LBM_ERR_UNSTABLE;
+    }
     return LBM_OK;
 }
 
@@ -550,7 +704,7 @@ int lbm_reduce(lbm_ctx *c, double *out)
     memcpy(&errword, (const char *)r + 64, sizeof(errword));
     if (errword != 0)
         return LBM_ERR_CUDA;
-    out[0] = r[0] + (c->shifted ? (double)c->N : 0.0);
+    out[0] = r[0] + (c->shifted ? (double)c->n_fluid : 0.0);
     out[1] = r[1];
     out[2] = r[2];
     out[3] = r[3];

@@ -34,6 +34,13 @@ struct lbm_ctx {
     int kernel_variant;  // lbm_kernel_variant
     int num_sms;         // queried at the first staged launch
     unsigned *err;       // error word of the bounded waits (in the workspace)
+    // per-face boundaries and obstacles (the general step kernel)
+    bool geo;                   // LBM_BC_FACES or obstacles
+    int face[6];                // lbm_face per face
+    unsigned *links;            // per-node link words (workspace), or NULL
+    bool links_ready;           // lbm_set_geometry has run
+    unsigned long long *count;  // solid-node counter (workspace)
+    int64_t n_fluid;            // nodes that are not solid
     lbm::StepParams sp;
     // adjoint run recorded by lbm_adjoint_forward for lbm_adjoint_backward
     int64_t adj_T, adj_K;
@@ -46,7 +53,7 @@ namespace lbm {
 lbm::Launch ctx_base_launch(const lbm_ctx *c, int kind);
 cudaError_t ctx_dispatch(const lbm_ctx *c, const lbm::Launch &l);
 int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u_out,
-                    long long *reduce_blocks = nullptr);
+                    long long *reduce_blocks = nullptr, bool obstacle_force = false);
 int ctx_launch_moments(lbm_ctx *c, const void *src, int form, void *p_out, void *u_out,
                        int out_f32, double *partials);
 int ctx_current_form(const lbm_ctx *c);

@@ -47,6 +47,8 @@ struct Coef {
     R omega_m;   // TRT: relaxation rate of the antisymmetric part
     R kf_m;      // TRT: (1 - omega_m/2)/omega_m
     R lid[kMaxQ];  // 2 t_a rho0 (e_a . U)/c_s^2 for links crossing the moving wall
+    R pout2;       // outflow: 2 (P_out - sigma)
+    R pout_r;      // outflow: density of the even equilibrium (rho0, or P_out if compressible)
 };
 
 struct StepParams {
@@ -56,6 +58,11 @@ struct StepParams {
     int lid_on;    // the +y wall moves
     Coef<float> cf;
     Coef<double> cd;
+    // per-face boundaries and obstacles (general kernel, lbm_geo.cuh)
+    int face[6];            // lbm_face per face: -x, +x, -y, +y, -z, +z
+    const unsigned *links;  // per-node link word, or NULL (no obstacles)
+    const float *inlet;     // inlet velocity, d * (face nodes), or NULL (at rest)
+    int inlet_face;         // face index of the inlet, or -1
     double *partials;  // per-block monitor sums (RED kernels)
     const float *F;  // body force, d*N component-major (FORCE kernels)
     void *u_out;     // velocity output, d*N component-major, kernel arithmetic type (UOUT)
@@ -556,6 +563,7 @@ struct MomParams {
     double *partials;  // gridDim.x * kPartialStride doubles, or NULL
     int nseg;          // x-segments * ny * nz
     int xseg;          // x-segments per row
+    const unsigned *links;  // per-node link words: solid nodes report zero
 };
 
 template <class R>
@@ -595,8 +603,26 @@ __global__ void __launch_bounds__(256) k_moments(const typename Sto<S>::T *src, 
         const int y = row % p.ny, z = row / p.ny;
         const int x = xs * blockDim.x + threadIdx.x;
         R vals[kReduceVals] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-        if (x < p.nx) {
-            const int n = x + p.nx * (y + p.ny * z);
+        const int n0 = x + p.nx * (y + p.ny * z);
+        const bool solid = x < p.nx && m.links && (m.links[n0] >> 31);
+        if (solid) {
+            if (m.p_out) {
+                if (m.out_f32)
+                    ((float *)m.p_out)[n0] = 0.f;
+                else
+                    ((double *)m.p_out)[n0] = 0.0;
+            }
+            if (m.u_out) {
+                for (int k = 0; k < L::D; ++k) {
+                    if (m.out_f32)
+                        ((float *)m.u_out)[k * N + n0] = 0.f;
+                    else
+                        ((double *)m.u_out)[k * N + n0] = 0.0;
+                }
+            }
+        }
+        if (x < p.nx && !solid) {
+            const int n = n0;
             R g[Q];
             if constexpr (FORM == FORM_LOCAL) {
                 SFor<0, Q>::run([&](auto A_) {
@@ -764,7 +790,7 @@ struct AdjParams {
 };
 
 // ---- host-side launch descriptors ----------------------------------------------
-enum Kind { K_STEP = 0, K_INIT = 1, K_MOMENTS = 2, K_ADJ = 3, K_SEED = 4, K_FLUSH = 5 };
+enum Kind { K_STEP = 0, K_INIT = 1, K_MOMENTS = 2, K_ADJ = 3, K_SEED = 4, K_FLUSH = 5, K_LINKS = 6 };
 
 struct Launch {
     int kind;
@@ -781,6 +807,11 @@ struct Launch {
     size_t count;  // K_FLUSH
     bool bulk;     // K_STEP: use the shared-memory staged kernel (lbm_bulk.cuh)
     bool pair;     // K_STEP: two nodes per thread, 32-bit accesses (lbm_pair.cuh)
+    bool geo;      // K_STEP: the general kernel (per-face boundaries, obstacles; lbm_geo.cuh)
+    int mon;       // K_STEP with geo: 0, 1 = monitor sums, 2 = obstacle force sums
+    const unsigned char *solid;  // K_LINKS: N bytes, nonzero = solid
+    unsigned *links;             // K_LINKS: output link words
+    unsigned long long *nsolid;  // K_LINKS: number of solid nodes (added to)
     int bulk_nseg, bulk_xseg, num_sms;
     unsigned *err;  // error word for bounded waits
     dim3 grid, block;

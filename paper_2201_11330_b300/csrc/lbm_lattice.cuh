@@ -31,6 +31,11 @@ struct D2Q9 {
                : (e(a, 0) * e(a, 0) + e(a, 1) * e(a, 1)) == 1 ? 1.0 / 9.0
                                                               : 1.0 / 36.0;
     }
+    // direction number of the vector (ex, ey, ez)
+    __host__ __device__ static constexpr int index_of(int ex, int ey, int ez)
+    {
+        return 3 * (ex + 1) + (ey + 1) + 0 * ez;
+    }
 };
 
 struct D3Q27 {
@@ -46,6 +51,10 @@ struct D3Q27 {
     __host__ __device__ static constexpr double w(int a)
     {
         return s2(a) == 0 ? 8.0 / 27.0 : s2(a) == 1 ? 2.0 / 27.0 : s2(a) == 2 ? 1.0 / 54.0 : 1.0 / 216.0;
+    }
+    __host__ __device__ static constexpr int index_of(int ex, int ey, int ez)
+    {
+        return 9 * (ex + 1) + 3 * (ey + 1) + (ez + 1);
     }
 };
 
@@ -69,6 +78,12 @@ struct D3Q19 {
     {
         return D3Q27::s2(cube(a)) == 0 ? 1.0 / 3.0 : D3Q27::s2(cube(a)) == 1 ? 1.0 / 18.0 : 1.0 / 36.0;
     }
+    // cube index minus the corners (0, 2, 6, 8, 18, 20, 24, 26) before it
+    __host__ __device__ static constexpr int index_of(int ex, int ey, int ez)
+    {
+        const int c = D3Q27::index_of(ex, ey, ez);
+        return c - (c > 0) - (c > 2) - (c > 6) - (c > 8) - (c > 18) - (c > 20) - (c > 24);
+    }
 };
 
 template <class L>
@@ -85,6 +100,8 @@ constexpr bool check_set()
         for (int k = 0; k < 3; ++k)
             if (L::e(opp<L>(a), k) != -L::e(a, k))
                 return false;
+        if (L::index_of(L::e(a, 0), L::e(a, 1), L::e(a, 2)) != a)
+            return false;
         sw += L::w(a);
     }
     return sw > 1.0 - 1e-12 && sw < 1.0 + 1e-12;

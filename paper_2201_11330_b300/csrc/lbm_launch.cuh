@@ -4,6 +4,7 @@
 
 #include "lbm_adjoint.cuh"
 #include "lbm_bulk.cuh"
+#include "lbm_geo.cuh"
 #include "lbm_kernels.cuh"
 #include "lbm_pair.cuh"
 
@@ -94,6 +95,29 @@ cudaError_t launch_storage(const Launch &l)
                     });
                 });
             });
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
+    if (l.kind == K_STEP && l.geo) {
+        return with_model(l.model, [&](auto C) {
+            return with_bool(l.force, [&](auto Fo) {
+                constexpr int c = decltype(C)::value;
+                constexpr bool fo = decltype(Fo)::value;
+                if (l.mon == 1)
+                    k_step_geo<L, S, c, fo, 1><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                else if (l.mon == 2)
+                    k_step_geo<L, S, c, fo, 2><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                else
+                    k_step_geo<L, S, c, fo, 0><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                return cudaGetLastError();
+            });
+        });
+    }
+    if (l.kind == K_LINKS) {
+        if constexpr (S == ST_F32) {  // storage-independent: one instantiation per lattice
+            k_links<L><<<l.grid, l.block, 0, l.stream>>>(l.solid, l.links, l.nsolid, l.sp);
+            return cudaGetLastError();
         } else {
             return cudaErrorInvalidValue;
         }

@@ -213,6 +213,8 @@ extern "C" int lbm_reduce_state_noalloc(int lattice, int nx, int ny, int nz, int
     const lbm_opts &o = *opts;
     if (o.storage < LBM_F64 || o.storage > LBM_BF16S || !(o.rho0 > 0.0) || !isfinite(o.rho0))
         return LBM_ERR_ARG;
+    if (o.geometry)  // solid nodes are known only to a context
+        return LBM_ERR_ARG;
     // same launch shape as the context path: x-segments of up to 256 nodes
     int bx = (nx + 31) / 32 * 32;
     if (bx > 256)

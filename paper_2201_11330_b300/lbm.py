@@ -21,7 +21,10 @@ LIB_PATH = os.path.join(HERE, "liblbm.so")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_STATE, LBM_ERR_NOMEM = 0, -1, -2, -3, -4, -5
 LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 = 0, 1, 2
-LBM_BC_PERIODIC, LBM_BC_CAVITY, LBM_BC_CHANNEL = 0, 1, 2
+LBM_BC_PERIODIC, LBM_BC_CAVITY, LBM_BC_CHANNEL, LBM_BC_FACES = 0, 1, 2, 3
+LBM_FACE_PERIODIC, LBM_FACE_WALL, LBM_FACE_INLET, LBM_FACE_OUTFLOW, LBM_FACE_SYMMETRY = 0, 1, 2, 3, 4
+FACES = {"periodic": LBM_FACE_PERIODIC, "wall": LBM_FACE_WALL, "inlet": LBM_FACE_INLET,
+         "outflow": LBM_FACE_OUTFLOW, "symmetry": LBM_FACE_SYMMETRY}
 LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = 0, 1, 2, 3
 LBM_COLL_BGK, LBM_COLL_TRT = 0, 1
 LBM_KERNEL_AUTO, LBM_KERNEL_PLAIN, LBM_KERNEL_STAGED, LBM_KERNEL_PAIRED = 0, 1, 2, 3
@@ -36,7 +39,8 @@ QD = {LBM_D2Q9: (9, 2), LBM_D3Q19: (19, 3), LBM_D3Q27: (27, 3)}
 # Every extern "C" symbol include/lbm.h declares.
 EXPORTS = [
     "lbm_default_opts", "lbm_tau_from_paper", "lbm_workspace_bytes", "lbm_create",
-    "lbm_set_stream", "lbm_init", "lbm_set_force", "lbm_set_lid", "lbm_step",
+    "lbm_set_stream", "lbm_init", "lbm_set_force", "lbm_set_lid", "lbm_set_geometry",
+    "lbm_set_inlet", "lbm_step_force", "lbm_step",
     "lbm_step_count", "lbm_set_kernel_variant", "lbm_kernel_variant_in_use",
     "lbm_step_reduce", "lbm_macroscopic", "lbm_reduce", "lbm_state_bytes", "lbm_get_state",
     "lbm_set_state", "lbm_adjoint_workspace_bytes", "lbm_adjoint_forward",
@@ -49,7 +53,9 @@ class lbm_opts(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("aa", ctypes.c_int), ("compressible", ctypes.c_int),
                 ("f32_unshifted", ctypes.c_int), ("rho0", ctypes.c_double),
                 ("lid_u", ctypes.c_double * 3), ("has_force", ctypes.c_int),
-                ("collision", ctypes.c_int), ("trt_lambda", ctypes.c_double)]
+                ("collision", ctypes.c_int), ("trt_lambda", ctypes.c_double),
+                ("faces", ctypes.c_int * 6), ("geometry", ctypes.c_int),
+                ("p_outflow", ctypes.c_double)]
 
 
 class LBMError(RuntimeError):
@@ -86,6 +92,9 @@ def load():
         "lbm_init": (ip, [_vp, _vp, _vp]),
         "lbm_set_force": (ip, [_vp, _vp]),
         "lbm_set_lid": (ip, [_vp, _dp]),
+        "lbm_set_geometry": (ip, [_vp, _vp]),
+        "lbm_set_inlet": (ip, [_vp, _vp]),
+        "lbm_step_force": (ip, [_vp, _i64, _dp]),
         "lbm_step": (ip, [_vp, _i64]),
         "lbm_step_count": (_i64, [_vp]),
         "lbm_set_kernel_variant": (ip, [_vp, ip]),
@@ -151,6 +160,20 @@ def lbm_set_force(ctx, force_ptr):
 def lbm_set_lid(ctx, lid3):
     arr = (ctypes.c_double * 3)(*[float(v) for v in lid3])
     _check(load().lbm_set_lid(ctx, arr), "lbm_set_lid")
+
+
+def lbm_set_geometry(ctx, solid_ptr):
+    _check(load().lbm_set_geometry(ctx, solid_ptr), "lbm_set_geometry")
+
+
+def lbm_set_inlet(ctx, u_ptr):
+    _check(load().lbm_set_inlet(ctx, u_ptr), "lbm_set_inlet")
+
+
+def lbm_step_force(ctx, n: int):
+    out = (ctypes.c_double * 3)()
+    _check(load().lbm_step_force(ctx, int(n), out), "lbm_step_force")
+    return list(out)
 
 
 def lbm_step(ctx, n: int):
@@ -260,11 +283,16 @@ class Lattice:
     Fields exchanged with it are torch tensors on the same device: pressure
     (N,), velocity (d, N) in FP64 (or FP32 for outputs on request), force
     (d, N) in FP32.  Calls launch on torch's current stream.
+
+    ``bc`` is "periodic", "cavity", "channel" or six face types ("periodic",
+    "wall", "inlet", "outflow", "symmetry"; order -x, +x, -y, +y, -z, +z).
+    ``obstacles=True`` reserves the link words for ``set_geometry``.
     """
 
     def __init__(self, lattice, nx, ny, nz, tau, bc, *, storage="f32", aa=False,
                  compressible=False, f32_unshifted=False, rho0=1.0, lid=(0.0, 0.0, 0.0),
-                 has_force=False, kernel="auto", trt_lambda=None, device="cuda"):
+                 has_force=False, kernel="auto", trt_lambda=None, obstacles=False,
+                 p_outflow=1.0 / 3.0, device="cuda"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the LBM library needs a CUDA device")
@@ -274,9 +302,20 @@ class Lattice:
         self.shape = (int(nx), int(ny), int(nz))
         self.N = int(nx) * int(ny) * int(nz)
         self.tau = float(tau)
-        self.bc = _key(BCS, bc)
-        self.device = torch.device(device)
         o = lbm_default_opts()
+        if isinstance(bc, (str, int)):
+            self.bc = _key(BCS, bc)
+        else:  # six face types
+            faces = [_key(FACES, f) for f in bc]
+            if len(faces) != 6:
+                raise ValueError("six face types expected")
+            for i, f in enumerate(faces):
+                o.faces[i] = f
+            self.bc = LBM_BC_FACES
+        self.faces = [o.faces[i] for i in range(6)]
+        o.geometry = int(bool(obstacles))
+        o.p_outflow = float(p_outflow)
+        self.device = torch.device(device)
         o.storage = _key(STORAGES, storage)
         o.aa = int(bool(aa))
         o.compressible = int(bool(compressible))
@@ -297,6 +336,7 @@ class Lattice:
         self.ctx = lbm_create(self.lattice, nx, ny, nz, self.tau, self.bc, o,
                               self.workspace.data_ptr(), nbytes, self._stream())
         self._force = None
+        self._inlet = None
         self._adj_ws = None
         if kernel != "auto":
             self.set_kernel(kernel)
@@ -341,6 +381,38 @@ class Lattice:
     def set_lid(self, lid):
         lbm_set_lid(self.ctx, list(lid) + [0.0] * (3 - len(lid)))
         return self
+
+    def set_geometry(self, solid):
+        """Solid obstacles: N values, nonzero = solid (copied into link words).
+        The state must be initialised again afterwards."""
+        torch = self.torch
+        self._sync_stream()
+        st = torch.as_tensor(solid, device=self.device).reshape(-1).ne(0).to(torch.uint8)
+        if st.numel() != self.N:
+            raise ValueError(f"expected {self.N} values, got {st.numel()}")
+        lbm_set_geometry(self.ctx, st.data_ptr())
+        return self
+
+    def set_inlet(self, u):
+        """Inlet velocity (d, face nodes) FP32 (see lbm_set_inlet; None = at rest)."""
+        torch = self.torch
+        if u is None:
+            lbm_set_inlet(self.ctx, None)
+            self._inlet = None
+            return self
+        face = self.faces.index(LBM_FACE_INLET) if LBM_FACE_INLET in self.faces else 0
+        nx, ny, nz = self.shape
+        nf = {0: ny * nz, 1: nx * nz, 2: nx * ny}[face // 2]
+        ut = self._dev(u, torch.float32, self.d * nf)
+        lbm_set_inlet(self.ctx, ut.data_ptr())
+        self._inlet = ut
+        return self
+
+    def step_force(self, n=1):
+        """step(n); returns the momentum-exchange force on the obstacles (3,)
+        during the last step."""
+        self._sync_stream()
+        return lbm_step_force(self.ctx, n)
 
     def step(self, n=1):
         self._sync_stream()
