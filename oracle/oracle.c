@@ -434,10 +434,11 @@ static int resolve_link(const or_model *m, int x, int y, int z, int a, long *src
         return OR_LINK_SOLID;
     }
     /* the (possibly reflected) direction e */
-    int b = -1;
-    for (int i = 0; i < v->Q; ++i)
-        if (v->e[i][0] == e[0] && v->e[i][1] == e[1] && v->e[i][2] == e[2])
-            b = i;
+    int b = a;
+    if (e[0] != v->e[a][0] || e[1] != v->e[a][1] || e[2] != v->e[a][2])
+        for (int i = 0; i < v->Q; ++i)
+            if (v->e[i][0] == e[0] && v->e[i][1] == e[1] && v->e[i][2] == e[2])
+                b = i;
     *src = nu;
     *slot = b;
     return OR_LINK_STREAM;
@@ -501,12 +502,18 @@ static void propagate(const or_model *m, const double *fb, double *f)
 /* Momentum exchange (Sec. 5): force on the solid nodes during the
  * propagation fb -> f, sum over fluid nodes x and links a whose source is an
  * obstacle of 2 fb_abar(x) e_abar (the population leaving x towards the
- * solid and coming back reversed).  Serial, fixed order. */
+ * solid and coming back reversed).  Each z-plane is summed in a fixed order
+ * (planes in parallel), then the planes in order: the result does not
+ * depend on the thread count. */
 static void obstacle_force(const or_model *m, const double *fb, double out[3])
 {
     const or_dvm *v = &m->v;
     const int Q = v->Q;
+    double *plane = calloc((size_t)m->nz * 3, sizeof(double));
     out[0] = out[1] = out[2] = 0.0;
+    if (!plane)
+        return;
+#pragma omp parallel for schedule(static)
     for (int z = 0; z < m->nz; ++z)
         for (int y = 0; y < m->ny; ++y)
             for (int x = 0; x < m->nx; ++x) {
@@ -521,9 +528,13 @@ static void obstacle_force(const or_model *m, const double *fb, double out[3])
                         continue;
                     int b = v->opp[a];
                     for (int k = 0; k < 3; ++k)
-                        out[k] += 2.0 * fb[n * Q + b] * v->e[b][k];
+                        plane[3 * z + k] += 2.0 * fb[n * Q + b] * v->e[b][k];
                 }
             }
+    for (int z = 0; z < m->nz; ++z)
+        for (int k = 0; k < 3; ++k)
+            out[k] += plane[3 * z + k];
+    free(plane);
 }
 
 static void collide_all(const or_model *m, const double *f, double *fb)

@@ -263,3 +263,28 @@ def test_geometry_argument_checks():
     with pytest.raises(LBMError):  # only the plain kernel runs the general path
         lat.set_kernel("staged")
     assert lat.kernel == "plain"
+
+
+def test_sphere_512x128x128_matches_oracle_at_point_a():
+    """Sec. 5 "validation of GPU offloading" at the paper's own size: D3Q27,
+    512 x 128 x 128, sphere of radius 8 centred at (64, 64, 64), inlet on the
+    back face (-x), outflow on the front (+x), symmetry planes left/right
+    (y), periodic top/bottom (z).  FP64 on the GPU against the FP64 oracle on
+    the host: the whole field, point A = (72, 72, 72), and the drag."""
+    nx, ny, nz = 512, 128, 128
+    U = 0.05
+    sol = sphere(nx, ny, nz, (64, 64, 64), 8)
+    inl = np.zeros((3, ny * nz))
+    inl[0] = U
+    u0 = np.zeros((3, nx * ny * nz))
+    u0[0] = U
+    u0[:, sol.ravel() != 0] = 0
+    got, ref = run_pair("d3q27", (nx, ny, nz), 0.53, SPHERE3D, 12, storage="f64", solid=sol,
+                        inlet=inl, u0=u0, force_out=True)
+    eu, ep = field_errors(got, ref, U)
+    assert eu < 1e-12 and ep < 1e-11, (eu, ep)
+    a = 72 + nx * (72 + ny * 72)
+    assert np.abs(got[1][:, a] - ref[1][:, a]).max() < 1e-15
+    assert abs(got[0][a] - ref[0][a]) < 1e-15
+    assert np.abs(got[1][:, a] - U * np.array([1, 0, 0])).max() > 1e-6  # A sees the sphere
+    assert np.abs(got[2] - ref[2]).max() < 1e-12 * np.abs(ref[2]).max()
