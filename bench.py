@@ -233,6 +233,42 @@ def run_cavity(lattice, n, re, storage, aa, steps, warmup, world, device, trt_la
     return out
 
 
+def run_sphere(storage, steps, warmup, world, device):
+    """The paper's performance workload (Sec. 5-6): D3Q27 flow past a sphere,
+    512 x 128 x 128, radius 8 at (64, 64, 64), uniform inlet 0.05 on -x,
+    pressure outlet on +x, symmetry planes on y, periodic z; tau 0.53
+    (Re = 80 on the diameter).  General step kernel; bytes per node update
+    2 Q b + 4 (the link word)."""
+    import numpy as np
+    import torch
+    from paper_2201_11330_b300.lbm import Lattice
+    nx, ny, nz = 512, 128, 128
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    solid = ((x - 64) ** 2 + (y - 64) ** 2 + (z - 64) ** 2 <= 64).astype(np.uint8)
+    lat = Lattice("d3q27", nx, ny, nz, 0.53,
+                  ["inlet", "outflow", "symmetry", "symmetry", "periodic", "periodic"],
+                  storage=storage, obstacles=True)
+    lat.set_geometry(torch.from_numpy(solid.ravel()).to(device))
+    u_in = torch.zeros((3, ny * nz), dtype=torch.float32, device=device)
+    u_in[0] = 0.05
+    lat.set_inlet(u_in)
+    u0 = torch.zeros((3, nx * ny * nz), dtype=torch.float64, device=device)
+    u0[0] = 0.05
+    u0[:, torch.from_numpy(solid.ravel() != 0).to(device)] = 0
+    lat.init(None, u0)
+    del u0
+    total, durs, _ = timed_steps(lat, steps, warmup, world)
+    total = max_over_ranks(total, world, device)
+    N = nx * ny * nz
+    f = lat.step_force(1)
+    bpn = 2 * 27 * BYTES_OF[storage] + 4
+    out = {"glups": replica_value(N, steps, total, world), "ms_per_step": total / steps,
+           "bytes_per_node": bpn, "nodes": N, "drag_force_x": f[0]}
+    del lat
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_e2e(n, re, storage, steps, warmup, world, device):
     """Public API with host buffers: pinned-host initial fields -> device,
     lbm_init, then per step lbm_step_reduce (the step with the Monitor fused
@@ -456,6 +492,10 @@ def main():
                        args.warmup, world, device)
         r["hbm_frac"] = r["glups"] / world * r["bytes_per_node"] / peak
         extras["d3q27_f16s_aa_768"] = r
+        for st in ("f64", "f32", "f16s"):
+            r = run_sphere(st, max(10, args.steps // 2), args.warmup, world, device)
+            r["hbm_frac"] = r["glups"] / world * r["bytes_per_node"] / peak
+            extras[f"sphere_d3q27_512x128x128_{st}"] = r
         try:
             extras["adjoint"] = run_adjoint(128, 2000, 100, world, device)
         except Exception as exc:  # reported, not hidden

@@ -195,18 +195,29 @@ __device__ __forceinline__ void geo_node(const typename Sto<S>::T *src, typename
         ubb = o_fma(ub[2], ub[2], o_fma(ub[1], ub[1], o_mul(ub[0], ub[0])));
     }
 
-    R g[Q];
+    // all loads first (straight-line, so every one is in flight before the
+    // first value is decoded), then the boundary terms
+    using T = typename Sto<S>::T;
+    T raw[Q];
     SFor<0, Q>::run([&](auto A_) {
         constexpr int a = decltype(A_)::value;
         constexpr int b = opp<L>(a);
+        int off, slot;
+        unsigned kind;
+        link_of<L, a>(X, Y, Z, off, kind, slot);
+        const bool own = (kind & (SK_BOUNCE | SK_OUT)) || ((lw >> a) & 1u);
+        raw[a] = ld(own ? src + b * N + n : src + (size_t)slot * N + (n + off));
+    });
+    R g[Q];
+    SFor<0, Q>::run([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
         constexpr int ex = L::e(a, 0), ey = L::e(a, 1), ez = L::e(a, 2);
         const R t = R(L::w(a));
         int off, slot;
         unsigned kind;
         link_of<L, a>(X, Y, Z, off, kind, slot);
-        R v;
+        R v = Sto<S>::dec(raw[a]);
         if (kind & SK_BOUNCE) {
-            v = Sto<S>::dec(src[b * N + n]);
             if (kind & SK_INLET) {
                 const R eu = R(ex) * uin[0] + R(ey) * uin[1] + R(ez) * uin[2];
                 v = o_fma(o_mul(R(6.0 * L::w(a)), c.rho0), eu, v);
@@ -216,10 +227,8 @@ __device__ __forceinline__ void geo_node(const typename Sto<S>::T *src, typename
         } else if (kind & SK_OUT) {
             const R eu = R(ex) * ub[0] + R(ey) * ub[1] + R(ez) * ub[2];
             const R q = o_fma(o_mul(R(4.5), eu), eu, o_mul(R(-1.5), ubb));
-            v = o_fma(t, c.pout2,
-                      o_fma(o_mul(R(2.0 * L::w(a)), c.pout_r), q, -Sto<S>::dec(src[b * N + n])));
+            v = o_fma(t, c.pout2, o_fma(o_mul(R(2.0 * L::w(a)), c.pout_r), q, -v));
         } else if ((lw >> a) & 1u) {
-            v = Sto<S>::dec(src[b * N + n]);
             if constexpr (MON == 2) {
                 // f*_b(x) leaves towards the solid and returns reversed
                 const R fb2 = o_mul(R(2), o_fma(c.sigma, t, v));
@@ -230,8 +239,6 @@ __device__ __forceinline__ void geo_node(const typename Sto<S>::T *src, typename
                 if constexpr (ez != 0)
                     fo[2] = o_fma(R(-ez), fb2, fo[2]);
             }
-        } else {
-            v = Sto<S>::dec(src[(size_t)slot * N + (n + off)]);
         }
         g[a] = v;
     });
