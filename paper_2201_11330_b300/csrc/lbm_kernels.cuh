@@ -379,11 +379,18 @@ __device__ __forceinline__ void block_monitor(const R (&mon)[6], double *partial
 // ---- one node of one time step ----------------------------------------------
 // INTERIOR: the node's row has neighbours inside the box in y and z (no wall,
 // no wrap), so only the x axis needs per-thread boundary logic.
+// EARLY_RED (with RED): reduce the monitor values across the warp right after
+// the collision and park the warp's sums in wsh[warp], so that they are not
+// held in registers through the stores (the AA gather half's push stores
+// otherwise take the kernel from 48 to 75 registers); every lane must then
+// run the node, idle lanes (active = false) on a copy of a real node, storing
+// nothing.
 template <class L, int S, int PAT, int MODEL, bool FORCE, bool UOUT, bool INTERIOR,
-          bool RED = false>
+          bool RED = false, bool EARLY_RED = false>
 __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typename Sto<S>::T *dst,
                                           const StepParams &p, int x, int y, int z,
-                                          typename Sto<S>::R (&mon)[6])
+                                          typename Sto<S>::R (&mon)[6], bool active = true,
+                                          double (*wsh)[6] = nullptr)
 {
     using T = typename Sto<S>::T;
     using R = typename Sto<S>::R;
@@ -423,7 +430,11 @@ __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typenam
                 ptr = wall ? src + b * N + n : src + a * N + (n + off);
             else
                 ptr = wall ? src + a * N + n : src + b * N + (n + off);
-            R v = Sto<S>::dec(ld(ptr));
+            R v;
+            if constexpr (EARLY_RED)  // an idle lane reads nothing (the slots are owned)
+                v = active ? Sto<S>::dec(ld(ptr)) : R(0);
+            else
+                v = Sto<S>::dec(ld(ptr));
             if constexpr (L::e(a, 1) == -1) {
                 if (lid_row)
                     v += c.lid[a];
@@ -442,6 +453,17 @@ __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typenam
     collide<L, R, MODEL, FORCE>(g, F, c, u, s_, rho_);
     if constexpr (RED)
         monitor_values(s_, rho_, u, mon);
+    if constexpr (RED && EARLY_RED) {
+        R w[6];
+        for (int k = 0; k < 5; ++k)
+            w[k] = warp_sum(active ? mon[k] : R(0));
+        w[5] = warp_max(active ? mon[5] : R(0));
+        if ((threadIdx.x & 31) == 0)
+            for (int k = 0; k < 6; ++k)
+                wsh[threadIdx.x >> 5][k] = double(w[k]);
+        if (!active)
+            return;
+    }
     if constexpr (UOUT) {
         SFor<0, L::D>::run([&](auto K_) {
             constexpr int k = decltype(K_)::value;
@@ -472,12 +494,9 @@ __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typenam
 }
 
 // grid: (ceil(nx/blockDim.x), ny, nz); one node per thread.
-template <class L, int S, int PAT, int MODEL, bool FORCE, bool UOUT, bool RED = false>
-// (__launch_bounds__ with an explicit minimum of 1 block lets nvcc roughly
-// double the register count of these kernels and halves their occupancy;
-// the thread bound alone keeps them at 40-48 registers.)
-__global__ void __launch_bounds__(256) k_step(const typename Sto<S>::T *src,
-                                              typename Sto<S>::T *dst, const StepParams p)
+template <class L, int S, int PAT, int MODEL, bool FORCE, bool UOUT, bool RED>
+__device__ __forceinline__ void step_kernel_body(const typename Sto<S>::T *src,
+                                                 typename Sto<S>::T *dst, const StepParams &p)
 {
     using R = typename Sto<S>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -487,6 +506,31 @@ __global__ void __launch_bounds__(256) k_step(const typename Sto<S>::T *src,
             return;
     }
     R mon[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    if constexpr (RED && PAT == PAT_GATHER) {
+        // warp sums before the stores (see EARLY_RED); idle lanes recompute
+        // the row's last node
+        __shared__ double wsh[8][6];
+        const bool active = x < p.nx;
+        const int xc = active ? x : p.nx - 1;
+        const bool interior = y > 0 && y < p.ny - 1 && (L::D == 2 || (z > 0 && z < p.nz - 1));
+        if (interior)
+            step_node<L, S, PAT, MODEL, FORCE, UOUT, true, true, true>(src, dst, p, xc, y, z, mon,
+                                                                       active, wsh);
+        else
+            step_node<L, S, PAT, MODEL, FORCE, UOUT, false, true, true>(src, dst, p, xc, y, z, mon,
+                                                                        active, wsh);
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            const int k = threadIdx.x, nw = (blockDim.x + 31) >> 5;
+            double r = wsh[0][k];
+            for (int i = 1; i < nw; ++i)
+                r = (k == 5) ? fmax(r, wsh[i][k]) : r + wsh[i][k];
+            const size_t b =
+                blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+            p.partials[b * kPartialStride + k] = r;
+        }
+        return;
+    }
     if (x < p.nx) {
         if constexpr (PAT == PAT_LOCAL) {
             step_node<L, S, PAT, MODEL, FORCE, UOUT, true, RED>(src, dst, p, x, y, z, mon);
@@ -501,6 +545,26 @@ __global__ void __launch_bounds__(256) k_step(const typename Sto<S>::T *src,
     }
     if constexpr (RED)
         block_monitor(mon, p.partials);
+}
+
+// (__launch_bounds__ with an explicit minimum of 1 block lets nvcc roughly
+// double the register count of these kernels and halves their occupancy;
+// the thread bound alone keeps them at 40-48 registers.)
+template <class L, int S, int PAT, int MODEL, bool FORCE, bool UOUT, bool RED = false>
+__global__ void __launch_bounds__(256) k_step(const typename Sto<S>::T *src,
+                                              typename Sto<S>::T *dst, const StepParams p)
+{
+    step_kernel_body<L, S, PAT, MODEL, FORCE, UOUT, RED>(src, dst, p);
+}
+
+// The AA gather half with the monitor fused in: held to five blocks per SM
+// (48 registers, a few bytes spilled) instead of the 62 it takes unbounded.
+template <class L, int S, int MODEL, bool FORCE>
+__global__ void __launch_bounds__(256, 5) k_step_gather_red(const typename Sto<S>::T *src,
+                                                            typename Sto<S>::T *dst,
+                                                            const StepParams p)
+{
+    step_kernel_body<L, S, PAT_GATHER, MODEL, FORCE, false, true>(src, dst, p);
 }
 
 // ---- initialisation (Sec. 2.2: f = feq(p, u), then the first collision) -----

@@ -158,11 +158,13 @@ cudaError_t launch_storage(const Launch &l)
         if (l.pattern == PAT_GATHER) {
             return with_model(l.model, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
-                    return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
+                    if (l.sp.partials != nullptr)
+                        k_step_gather_red<L, S, decltype(C)::value, decltype(Fo)::value>
+                            <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                    else
                         k_step<L, S, PAT_GATHER, decltype(C)::value, decltype(Fo)::value, false,
-                               decltype(Rd)::value><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
-                        return cudaGetLastError();
-                    });
+                               false><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                    return cudaGetLastError();
                 });
             });
         }
