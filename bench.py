@@ -422,6 +422,8 @@ def main():
                     help="cavity side of the headline run (profiling uses smaller boxes)")
     ap.add_argument("--storage", default=HEADLINE["storage"], choices=list(BYTES_OF),
                     help="storage of the headline run (profiling of the other variants)")
+    ap.add_argument("--workload", default="cavity", choices=["cavity", "sphere"],
+                    help="sphere: only the paper's D3Q27 sphere flow at --storage (profiling)")
     ap.add_argument("--no-extras", action="store_true",
                     help="headline line only (no storage variants, D3Q27, adjoint, CPU)")
     args = ap.parse_args()
@@ -443,6 +445,13 @@ def main():
     if rank == 0:
         build.build()
     barrier(world)
+
+    if args.workload == "sphere":
+        r = run_sphere(args.storage, args.steps, args.warmup, world, device)
+        if rank == 0:
+            print(json.dumps({"workload": "D3Q27 sphere 512x128x128", "storage": args.storage,
+                              "steps": args.steps, "warmup": args.warmup, **r}))
+        return 0
 
     hb = dict(HEADLINE)
     hb["n"] = args.size
