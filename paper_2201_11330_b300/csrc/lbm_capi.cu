@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "lbm.h"
 #include "lbm_bulk.cuh"
@@ -95,8 +96,19 @@ bool resolve_faces(int lattice, int bc, const lbm_opts &o, int face[6])
     return ninlet <= 1;
 }
 
+// Boxes that may have open faces or obstacles keep a list of the nodes the
+// plain kernel cannot update (the general kernel takes those).
+bool wants_node_list(const lbm_opts &o)
+{
+    bool open = o.geometry != 0;
+    for (int i = 0; i < 6; ++i)
+        open = open || o.faces[i] != LBM_FACE_PERIODIC;
+    return open;
+}
+
 struct Layout {
     size_t state_bytes, f_off[2], partial_off, result_off, step_partial_off, links_off, total;
+    size_t flags_off, nlist_off;
     int nred;
     long long step_blocks;
 };
@@ -122,11 +134,21 @@ Layout layout_for(int lattice, int nx, int ny, int nz, const lbm_opts &o)
     // one monitor partial per block of a step launch (the plain kernel has the
     // most blocks of all step kernels)
     L.step_blocks = nseg;
+    long long parts = nseg;
+    if (wants_node_list(o))  // plus the general kernel's node-list blocks
+        parts += ((long long)N + 255) / 256;
     L.step_partial_off = off;
-    off += align_up((size_t)L.step_blocks * kPartialStride * sizeof(double));
+    off += align_up((size_t)parts * kPartialStride * sizeof(double));
     L.links_off = off;
     if (o.geometry)
         off += align_up(N * sizeof(unsigned));
+    L.flags_off = off;
+    L.nlist_off = off;
+    if (wants_node_list(o)) {
+        off += align_up(N);
+        L.nlist_off = off;
+        off += align_up(N * sizeof(int));
+    }
     L.total = off;
     return L;
 }
@@ -162,7 +184,18 @@ void fill_params(lbm_ctx *c)
     p.ny = c->ny;
     p.nz = c->nz;
     p.N = (int)c->N;
-    p.periodic = c->bc == LBM_BC_PERIODIC ? 7 : c->bc == LBM_BC_CHANNEL ? 5 : 0;
+    p.periodic = 0;
+    for (int k = 0; k < 3; ++k)
+        if (c->face[2 * k] == LBM_FACE_PERIODIC)
+            p.periodic |= 1 << k;
+    p.nlist = nullptr;
+    p.nlist_len = 0;
+    p.part_base = 0;
+    p.open_faces = 0;
+    for (int i = 0; i < 6; ++i)
+        if (c->face[i] == LBM_FACE_INLET || c->face[i] == LBM_FACE_OUTFLOW ||
+            c->face[i] == LBM_FACE_SYMMETRY)
+            p.open_faces |= 1 << i;
     p.lid_on = c->face[3] == LBM_FACE_WALL;
     p.inlet_face = -1;
     for (int i = 0; i < 6; ++i) {
@@ -270,6 +303,35 @@ namespace lbm {
 
 Launch ctx_base_launch(const lbm_ctx *c, int kind) { return base_launch(c, kind); }
 
+// Lists the nodes the plain kernel cannot update (solid, obstacle links,
+// open faces).  Once per geometry; synchronises.
+int build_node_list(lbm_ctx *c)
+{
+    const size_t N = (size_t)c->N;
+    Launch l = base_launch(c, K_FLAGS);
+    l.storage = LBM_F32;  // the flag kernel is instantiated once per lattice
+    l.flags = c->nflags;
+    if (dispatch(c->lattice, l) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    std::vector<unsigned char> flags(N);
+    if (cudaMemcpyAsync(flags.data(), c->nflags, N, cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    std::vector<int> list;
+    for (size_t n = 0; n < N; ++n)
+        if (flags[n])
+            list.push_back((int)n);
+    if (!list.empty() &&
+        (cudaMemcpyAsync(c->nlist, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice,
+                         c->stream) != cudaSuccess ||
+         cudaStreamSynchronize(c->stream) != cudaSuccess))
+        return LBM_ERR_CUDA;
+    c->n_general = (long long)list.size();
+    c->list_ready = true;
+    return LBM_OK;
+}
+
 cudaError_t ctx_dispatch(const lbm_ctx *c, const Launch &l) { return dispatch(c->lattice, l); }
 
 int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u_out,
@@ -282,12 +344,44 @@ int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u
     if (reduce_blocks)
         l.sp.partials = c->step_partials;
     if (c->geo) {
-        // the general kernel: pull scheme, one node per thread
-        l.geo = true;
-        l.mon = reduce_blocks ? (obstacle_force ? 2 : 1) : 0;
+        // pull scheme, one node per thread: the plain kernel on every node
+        // it can update (walls, lid, periodic faces; same arithmetic, bitwise
+        // equal results), the general kernel on the listed rest
+        const int mon = reduce_blocks ? (obstacle_force ? 2 : 1) : 0;
+        const long long grid_blocks = (long long)l.grid.x * l.grid.y * l.grid.z;
+        if (!c->nflags) {
+            l.geo = true;
+            l.mon = mon;
+            if (reduce_blocks)
+                *reduce_blocks = grid_blocks;
+            return dispatch(c->lattice, l) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+        }
+        if (!c->list_ready) {
+            const int rc = build_node_list(c);
+            if (rc != LBM_OK)
+                return rc;
+        }
+        const long long gblocks = (c->n_general + 255) / 256;
+        if (gblocks > 0) {
+            Launch lg = l;
+            lg.geo = true;
+            lg.mon = mon;
+            lg.sp.nlist = c->nlist;
+            lg.sp.nlist_len = (int)c->n_general;
+            lg.sp.part_base = grid_blocks;
+            lg.grid = dim3((unsigned)gblocks, 1, 1);
+            lg.block = dim3(256, 1, 1);
+            if (dispatch(c->lattice, lg) != cudaSuccess)
+                return LBM_ERR_CUDA;
+        }
+        Launch ls = l;
+        ls.skip = true;
+        ls.mon = mon;
+        if (dispatch(c->lattice, ls) != cudaSuccess)
+            return LBM_ERR_CUDA;
         if (reduce_blocks)
-            *reduce_blocks = (long long)l.grid.x * l.grid.y * l.grid.z;
-        return dispatch(c->lattice, l) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+            *reduce_blocks = grid_blocks + gblocks;
+        return LBM_OK;
     }
     if (u_out) {
         l.uout = true;
@@ -443,6 +537,9 @@ int lbm_create(int lattice, int nx, int ny, int nz, double tau, int bc, const lb
     c->links_ready = false;
     c->count = (unsigned long long *)((char *)c->result + 128);
     c->n_fluid = c->N;
+    c->nflags = wants_node_list(o) ? (unsigned char *)(c->ws + L.flags_off) : nullptr;
+    c->nlist = wants_node_list(o) ? (int *)(c->ws + L.nlist_off) : nullptr;
+    c->list_ready = false;
     fill_params(c);
     c->sp.inlet = nullptr;
     *out = c;
@@ -528,6 +625,7 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *solid)
     c->n_fluid = c->N - (int64_t)nsolid;
     c->links_ready = true;
     c->sp.links = c->links;
+    c->list_ready = false;  // the general kernel's nodes change with the obstacles
     c->initialized = false;
     return LBM_OK;
 }

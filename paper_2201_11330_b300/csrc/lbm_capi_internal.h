@@ -41,6 +41,10 @@ struct lbm_ctx {
     bool links_ready;           // lbm_set_geometry has run
     unsigned long long *count;  // solid-node counter (workspace)
     int64_t n_fluid;            // nodes that are not solid
+    unsigned char *nflags;      // per-node "needs the general kernel" flags (workspace)
+    int *nlist;                 // the nodes that need the general kernel (workspace)
+    bool list_ready;
+    long long n_general;        // entries of nlist
     lbm::StepParams sp;
     // adjoint run recorded by lbm_adjoint_forward for lbm_adjoint_backward
     int64_t adj_T, adj_K;

@@ -260,27 +260,57 @@ __global__ void __launch_bounds__(256) k_step_geo(const typename Sto<S>::T *src,
                                                   typename Sto<S>::T *dst, const StepParams p)
 {
     using R = typename Sto<S>::R;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if constexpr (MON == 0) {
-        if (x >= p.nx)
-            return;
-    }
     R mon[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     R fo[3] = {R(0), R(0), R(0)};
-    if (x < p.nx) {
-        const bool interior = y > 0 && y < p.ny - 1 && (L::D == 2 || (z > 0 && z < p.nz - 1));
-        if (interior)
-            geo_node<L, S, MODEL, FORCE, MON, true>(src, dst, p, x, y, z, mon, fo);
-        else
-            geo_node<L, S, MODEL, FORCE, MON, false>(src, dst, p, x, y, z, mon, fo);
+    size_t bid;
+    if (p.nlist) {
+        // one thread per listed node (rows mixed within a warp: general axes)
+        bid = (size_t)p.part_base + blockIdx.x;
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if constexpr (MON == 0) {
+            if (i >= p.nlist_len)
+                return;
+        }
+        if (i < p.nlist_len) {
+            const int n = p.nlist[i];
+            const int x = n % p.nx, row = n / p.nx;
+            geo_node<L, S, MODEL, FORCE, MON, false>(src, dst, p, x, row % p.ny, row / p.ny, mon,
+                                                     fo);
+        }
+    } else {
+        bid = grid_block_index();
+        const int x = blockIdx.x * blockDim.x + threadIdx.x;
+        const int y = blockIdx.y, z = blockIdx.z;
+        if constexpr (MON == 0) {
+            if (x >= p.nx)
+                return;
+        }
+        if (x < p.nx) {
+            const bool interior = y > 0 && y < p.ny - 1 && (L::D == 2 || (z > 0 && z < p.nz - 1));
+            if (interior)
+                geo_node<L, S, MODEL, FORCE, MON, true>(src, dst, p, x, y, z, mon, fo);
+            else
+                geo_node<L, S, MODEL, FORCE, MON, false>(src, dst, p, x, y, z, mon, fo);
+        }
     }
     if constexpr (MON == 1)
-        block_monitor(mon, p.partials);
+        block_monitor(mon, p.partials, bid);
     if constexpr (MON == 2) {
         R v[6] = {fo[0], fo[1], fo[2], R(0), R(0), R(0)};
-        block_monitor(v, p.partials);
+        block_monitor(v, p.partials, bid);
     }
+}
+
+// flags[n] = 1 for the nodes the plain kernel cannot update (needs_general).
+template <class L>
+__global__ void __launch_bounds__(256) k_node_flags(unsigned char *flags, const StepParams p)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= p.nx)
+        return;
+    const int n = x + p.nx * (y + p.ny * z);
+    flags[n] = needs_general(p, n, x, y, z) ? 1 : 0;
 }
 
 // Link words from a solid mask: bit 31 = the node is solid; bit a = the

@@ -63,6 +63,10 @@ struct StepParams {
     const unsigned *links;  // per-node link word, or NULL (no obstacles)
     const float *inlet;     // inlet velocity, d * (face nodes), or NULL (at rest)
     int inlet_face;         // face index of the inlet, or -1
+    const int *nlist;       // general kernel on a node list: the nodes, or NULL (full grid)
+    int nlist_len;          // entries of nlist
+    long long part_base;    // node-list launches: first partial entry of their blocks
+    int open_faces;         // bit f: face f is an inlet, outflow or symmetry face
     double *partials;  // per-block monitor sums (RED kernels)
     const float *F;  // body force, d*N component-major (FORCE kernels)
     void *u_out;     // velocity output, d*N component-major, kernel arithmetic type (UOUT)
@@ -353,7 +357,7 @@ __device__ __forceinline__ R warp_max(R v);
 // arithmetic, across warps in FP64, fixed order), written to
 // partials[block * 8 + k].  Every thread of the block must call it.
 template <class R>
-__device__ __forceinline__ void block_monitor(const R (&mon)[6], double *partials)
+__device__ __forceinline__ void block_monitor(const R (&mon)[6], double *partials, size_t b)
 {
     __shared__ double sh[32][6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -371,7 +375,6 @@ __device__ __forceinline__ void block_monitor(const R (&mon)[6], double *partial
         double r = sh[0][k];
         for (int i = 1; i < nwarps; ++i)
             r = (k == 5) ? fmax(r, sh[i][k]) : r + sh[i][k];
-        const size_t b = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
         partials[b * kPartialStride + k] = r;
     }
 }
@@ -496,11 +499,11 @@ __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typenam
 // grid: (ceil(nx/blockDim.x), ny, nz); one node per thread.
 template <class L, int S, int PAT, int MODEL, bool FORCE, bool UOUT, bool RED>
 __device__ __forceinline__ void step_kernel_body(const typename Sto<S>::T *src,
-                                                 typename Sto<S>::T *dst, const StepParams &p)
+                                                 typename Sto<S>::T *dst, const StepParams &p,
+                                                 int bx, int y, int z, size_t bid)
 {
     using R = typename Sto<S>::R;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int x = bx * blockDim.x + threadIdx.x;
     if constexpr (!RED) {  // no block-wide step follows: idle threads may leave
         if (x >= p.nx)
             return;
@@ -525,9 +528,7 @@ __device__ __forceinline__ void step_kernel_body(const typename Sto<S>::T *src,
             double r = wsh[0][k];
             for (int i = 1; i < nw; ++i)
                 r = (k == 5) ? fmax(r, wsh[i][k]) : r + wsh[i][k];
-            const size_t b =
-                blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
-            p.partials[b * kPartialStride + k] = r;
+            p.partials[bid * kPartialStride + k] = r;
         }
         return;
     }
@@ -544,7 +545,12 @@ __device__ __forceinline__ void step_kernel_body(const typename Sto<S>::T *src,
         }
     }
     if constexpr (RED)
-        block_monitor(mon, p.partials);
+        block_monitor(mon, p.partials, bid);
+}
+
+__device__ __forceinline__ size_t grid_block_index()
+{
+    return blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
 }
 
 // (__launch_bounds__ with an explicit minimum of 1 block lets nvcc roughly
@@ -554,7 +560,8 @@ template <class L, int S, int PAT, int MODEL, bool FORCE, bool UOUT, bool RED = 
 __global__ void __launch_bounds__(256) k_step(const typename Sto<S>::T *src,
                                               typename Sto<S>::T *dst, const StepParams p)
 {
-    step_kernel_body<L, S, PAT, MODEL, FORCE, UOUT, RED>(src, dst, p);
+    step_kernel_body<L, S, PAT, MODEL, FORCE, UOUT, RED>(src, dst, p, blockIdx.x, blockIdx.y,
+                                                         blockIdx.z, grid_block_index());
 }
 
 // The AA gather half with the monitor fused in: held to five blocks per SM
@@ -564,7 +571,54 @@ __global__ void __launch_bounds__(256, 5) k_step_gather_red(const typename Sto<S
                                                             typename Sto<S>::T *dst,
                                                             const StepParams p)
 {
-    step_kernel_body<L, S, PAT_GATHER, MODEL, FORCE, false, true>(src, dst, p);
+    step_kernel_body<L, S, PAT_GATHER, MODEL, FORCE, false, true>(
+        src, dst, p, blockIdx.x, blockIdx.y, blockIdx.z, grid_block_index());
+}
+
+// A node the plain kernel cannot update in a box with per-face boundaries or
+// obstacles: solid, with an obstacle link, or on an inlet, outflow or
+// symmetry face.
+__device__ __forceinline__ bool needs_general(const StepParams &p, int n, int x, int y, int z)
+{
+    const int f = p.open_faces;
+    bool open = ((f & 1) && x == 0) || ((f & 2) && x == p.nx - 1) || ((f & 4) && y == 0) ||
+                ((f & 8) && y == p.ny - 1) || ((f & 16) && z == 0) || ((f & 32) && z == p.nz - 1);
+    return open || (p.links && p.links[n] != 0u);
+}
+
+// The pull step of a box with per-face boundaries or obstacles on every node
+// the plain kernel can update (walls, lid and periodic faces only, no
+// obstacle link), which it computes exactly as the general kernel does; the
+// other nodes are left to the general kernel's node-list launch.  MON: 0,
+// 1 = monitor sums of these nodes, 2 = obstacle force (zero here).
+template <class L, int S, int MODEL, bool FORCE, int MON>
+__global__ void __launch_bounds__(256) k_step_skip(const typename Sto<S>::T *src,
+                                                   typename Sto<S>::T *dst, const StepParams p)
+{
+    using R = typename Sto<S>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int n = x + p.nx * (y + p.ny * z);
+    const bool active = x < p.nx && !needs_general(p, n, x, y, z);
+    if constexpr (MON == 2) {
+        if (threadIdx.x < kReduceVals)
+            p.partials[grid_block_index() * kPartialStride + threadIdx.x] = 0.0;
+    }
+    if constexpr (MON != 1) {
+        if (!active)
+            return;
+    }
+    R mon[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    if (active) {
+        const bool interior = y > 0 && y < p.ny - 1 && (L::D == 2 || (z > 0 && z < p.nz - 1));
+        if (interior)
+            step_node<L, S, PAT_PULL, MODEL, FORCE, false, true, MON == 1>(src, dst, p, x, y, z, mon);
+        else
+            step_node<L, S, PAT_PULL, MODEL, FORCE, false, false, MON == 1>(src, dst, p, x, y, z,
+                                                                            mon);
+    }
+    if constexpr (MON == 1)
+        block_monitor(mon, p.partials, grid_block_index());
 }
 
 // ---- initialisation (Sec. 2.2: f = feq(p, u), then the first collision) -----
@@ -854,7 +908,16 @@ struct AdjParams {
 };
 
 // ---- host-side launch descriptors ----------------------------------------------
-enum Kind { K_STEP = 0, K_INIT = 1, K_MOMENTS = 2, K_ADJ = 3, K_SEED = 4, K_FLUSH = 5, K_LINKS = 6 };
+enum Kind {
+    K_STEP = 0,
+    K_INIT = 1,
+    K_MOMENTS = 2,
+    K_ADJ = 3,
+    K_SEED = 4,
+    K_FLUSH = 5,
+    K_LINKS = 6,
+    K_FLAGS = 7
+};
 
 struct Launch {
     int kind;
@@ -872,7 +935,9 @@ struct Launch {
     bool bulk;     // K_STEP: use the shared-memory staged kernel (lbm_bulk.cuh)
     bool pair;     // K_STEP: two nodes per thread, 32-bit accesses (lbm_pair.cuh)
     bool geo;      // K_STEP: the general kernel (per-face boundaries, obstacles; lbm_geo.cuh)
-    int mon;       // K_STEP with geo: 0, 1 = monitor sums, 2 = obstacle force sums
+    bool skip;     // K_STEP: the plain pull kernel on the nodes it can update (k_step_skip)
+    int mon;       // K_STEP with geo or skip: 0, 1 = monitor sums, 2 = obstacle force sums
+    unsigned char *flags;        // K_FLAGS: one byte per node
     const unsigned char *solid;  // K_LINKS: N bytes, nonzero = solid
     unsigned *links;             // K_LINKS: output link words
     unsigned long long *nsolid;  // K_LINKS: number of solid nodes (added to)

@@ -114,6 +114,29 @@ cudaError_t launch_storage(const Launch &l)
             });
         });
     }
+    if (l.kind == K_STEP && l.skip) {
+        return with_model(l.model, [&](auto C) {
+            return with_bool(l.force, [&](auto Fo) {
+                constexpr int c = decltype(C)::value;
+                constexpr bool fo = decltype(Fo)::value;
+                if (l.mon == 1)
+                    k_step_skip<L, S, c, fo, 1><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                else if (l.mon == 2)
+                    k_step_skip<L, S, c, fo, 2><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                else
+                    k_step_skip<L, S, c, fo, 0><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                return cudaGetLastError();
+            });
+        });
+    }
+    if (l.kind == K_FLAGS) {
+        if constexpr (S == ST_F32) {  // storage-independent: one instantiation per lattice
+            k_node_flags<L><<<l.grid, l.block, 0, l.stream>>>(l.flags, l.sp);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     if (l.kind == K_LINKS) {
         if constexpr (S == ST_F32) {  // storage-independent: one instantiation per lattice
             k_links<L><<<l.grid, l.block, 0, l.stream>>>(l.solid, l.links, l.nsolid, l.sp);

@@ -454,7 +454,7 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
         }
     });
     if constexpr (RED)
-        block_monitor(mon, p.partials);
+        block_monitor(mon, p.partials, grid_block_index());
 }
 
 template <class L, int S, int PAT, int MODEL, bool FORCE, bool RED = false>
