@@ -127,3 +127,60 @@ def test_full_size_light_cone_samples(steps, storage, tol):
     d = np.abs(band - uc[:, None, :, None]).max() / U
     assert d < tol
     assert np.abs(uc[0]).max() > 1e-3  # the lid has started to drive the flow
+
+
+# ---------------------------------------------------------------------------
+# D3Q27 768^3, FP16-shifted AA storage (the bench's D3Q27 launch configuration)
+
+
+def _d3q27_768(steps):
+    from paper_2201_11330_b300.lbm import Lattice
+    n = 768
+    c = W.cavity_params(n, 2000.0, 0.1)
+    lat = Lattice("d3q27", n, n, n, c["tau"], "cavity", storage="f16s", aa=True, lid=c["lid"])
+    lat.init()
+    lat.step(steps)
+    return n, c, lat
+
+
+def test_d3q27_768_properties():
+    n, c, lat = _d3q27_768(120)
+    r = lat.reduce()
+    N = n ** 3
+    assert abs(r["mass"] - N) < 1e-4 * N
+    assert 0.05 < r["max_speed"] < 0.2
+    _, u = lat.macroscopic(torch.float32)
+    del lat
+    torch.cuda.empty_cache()
+    u = u.view(3, n, n, n)
+    assert (u[2] + u[2].flip(0)).abs().max().item() < 2e-4  # z-mirror symmetry
+    assert (u[0] - u[0].flip(0)).abs().max().item() < 2e-4
+    del u
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("steps", [6, 7])
+def test_d3q27_768_light_cone_samples(steps):
+    """After k steps from rest a node depends only on nodes within k of it: the
+    768^3 cavity's corner regions equal a 16^3 oracle cavity's, and its lid
+    interior equals a 1 x 16 x 1 oracle channel under the same lid."""
+    n, c, lat = _d3q27_768(steps)
+    _, u = lat.macroscopic(torch.float32)
+    del lat
+    u = u.view(3, n, n, n)
+    U, m, r = 0.1, 16, 8
+    _, uo = oracle.run("d3q27", m, m, m, c["tau"], "cavity", steps, lid=c["lid"])
+    uo = uo.reshape(3, m, m, m)
+    for ys_small, ys_big in ((slice(0, r + 1), slice(0, r + 1)), (slice(m - r - 1, m),
+                                                                   slice(n - r - 1, n))):
+        for xs_small, xs_big in ((slice(0, r + 1), slice(0, r + 1)), (slice(m - r - 1, m),
+                                                                       slice(n - r - 1, n))):
+            big = u[:, 0:r + 1, ys_big, xs_big].double().cpu().numpy()
+            d = np.abs(big - uo[:, 0:r + 1, ys_small, xs_small]).max() / U
+            assert d < 2e-3, (ys_big, xs_big, d)
+    _, uc = oracle.run("d3q27", 1, m, 1, c["tau"], "channel", steps, lid=c["lid"])
+    band = u[:, 300:460:23, n - m:, 300:460:19].double().cpu().numpy()
+    assert np.abs(band - uc[:, None, :, None]).max() / U < 2e-3
+    assert np.abs(uc[0]).max() > 1e-3
+    del u
+    torch.cuda.empty_cache()
