@@ -25,9 +25,9 @@ D2Q9, D3Q19, D3Q27 = 0, 1, 2
 BC_PERIODIC, BC_CAVITY, BC_CHANNEL = 0, 1, 2
 _LATTICE_NAMES = {"d2q9": D2Q9, "d3q19": D3Q19, "d3q27": D3Q27}
 _BC_NAMES = {"periodic": BC_PERIODIC, "cavity": BC_CAVITY, "channel": BC_CHANNEL}
-FACE_PERIODIC, FACE_WALL, FACE_INLET, FACE_OUTFLOW, FACE_SYMMETRY = 0, 1, 2, 3, 4
+FACE_PERIODIC, FACE_WALL, FACE_INLET, FACE_OUTFLOW, FACE_SYMMETRY, FACE_NODAL = 0, 1, 2, 3, 4, 5
 _FACE_NAMES = {"periodic": FACE_PERIODIC, "wall": FACE_WALL, "inlet": FACE_INLET,
-               "outflow": FACE_OUTFLOW, "symmetry": FACE_SYMMETRY}
+               "outflow": FACE_OUTFLOW, "symmetry": FACE_SYMMETRY, "nodal": FACE_NODAL}
 
 _lib = None
 
@@ -167,7 +167,7 @@ def run(lattice, nx, ny, nz, tau, bc, steps, *, rho0=1.0, compressible=False, li
     ``trt_lambda`` selects the two-relaxation-time collision.
 
     ``bc`` is "periodic", "cavity", "channel" or a sequence of six face
-    types ("periodic", "wall", "inlet", "outflow", "symmetry"; order -x, +x,
+    types ("periodic", "wall", "inlet", "outflow", "symmetry", "nodal"; order -x, +x,
     -y, +y, -z, +z).  ``solid``: N bytes, nonzero = obstacle node.
     ``inlet``: inlet velocity, shape (d, face nodes), the face's nodes
     numbered by its two remaining axes, lower axis fastest.  ``p_outflow``:

@@ -55,8 +55,15 @@
  *     printed; a velocity inlet needs a pressure level fixed somewhere, and a
  *     zero-gradient outlet leaves it free to drift); symmetry mirrors the
  *     coordinate back to that of x and reflects the direction's component
- *     normal to the face (specular, free slip).  Crossings rank wall/inlet,
- *     then outflow, then symmetry/periodic.  If the node so found is solid, the
+ *     normal to the face (specular, free slip); nodal is the paper's own
+ *     "modified nodal bounce-back" of Sec. 2.2 (Eq. (bb), Ziegler): the wall
+ *     lies on the boundary nodes, which collide like the bulk, and a
+ *     population entering one from outside is the one of the opposite
+ *     direction that has just arrived there from inside, f_a(x) = f_abar(x)
+ *     after propagation (plus the lid term on the +y face; where that
+ *     opposite population comes from outside too, as at a corner, the
+ *     node's own f*_abar(x) is taken).  Crossings rank wall/inlet, then
+ *     nodal, then outflow, then symmetry/periodic.  If the node so found is solid, the
  *     population bounces back at x as well (stationary obstacle), and the
  *     link's momentum exchange 2 f*_abar(x) e_abar counts towards the
  *     force on the obstacle (Sec. 5, momentum exchange of Ladd).  Solid
@@ -86,8 +93,9 @@
 enum { OR_D2Q9 = 0, OR_D3Q19 = 1, OR_D3Q27 = 2 };
 enum { OR_BC_PERIODIC = 0, OR_BC_CAVITY = 1, OR_BC_CHANNEL = 2 };
 enum { OR_FACE_PERIODIC = 0, OR_FACE_WALL = 1, OR_FACE_INLET = 2, OR_FACE_OUTFLOW = 3,
-       OR_FACE_SYMMETRY = 4 };
-enum { OR_LINK_STREAM = 0, OR_LINK_WALL = 1, OR_LINK_SOLID = 2, OR_LINK_OUTFLOW = 3 };
+       OR_FACE_SYMMETRY = 4, OR_FACE_NODAL = 5 };
+enum { OR_LINK_STREAM = 0, OR_LINK_WALL = 1, OR_LINK_SOLID = 2, OR_LINK_OUTFLOW = 3,
+       OR_LINK_NODAL = 4 };
 enum { OR_OK = 0, OR_ERR_ARG = -1, OR_ERR_NOMEM = -5 };
 
 /* 1/c_s^2 for all three velocity sets (c_s^2 = c^2/3, c = 1). */
@@ -374,12 +382,23 @@ static void inlet_velocity(const or_model *m, int x, int y, int z, double U[3])
  * or a bounce (OR_LINK_WALL, OR_LINK_SOLID, OR_LINK_OUTFLOW) involving slot
  * abar of the node itself, with *term the moving-wall term of a wall or
  * inlet link. */
+static int resolve_link_at(const or_model *m, int x, int y, int z, int a, long *src, int *slot,
+                           double *term, int nested);
+
 static int resolve_link(const or_model *m, int x, int y, int z, int a, long *src, int *slot,
                         double *term)
 {
+    return resolve_link_at(m, x, y, z, a, src, slot, term, 0);
+}
+
+/* nested: resolving the opposite population for a nodal link (a nodal
+ * crossing there reports OR_LINK_NODAL without looking further). */
+static int resolve_link_at(const or_model *m, int x, int y, int z, int a, long *src, int *slot,
+                           double *term, int nested)
+{
     const or_dvm *v = &m->v;
     const int c[3] = {x, y, z}, L[3] = {m->nx, m->ny, m->nz};
-    int up[3], e[3], bounce = 0, inlet = 0, lid = 0, outflow = 0;
+    int up[3], e[3], bounce = 0, inlet = 0, lid = 0, outflow = 0, nodal = 0;
     for (int k = 0; k < 3; ++k) {
         e[k] = v->e[a][k];
         up[k] = c[k] - e[k];
@@ -402,6 +421,11 @@ static int resolve_link(const or_model *m, int x, int y, int z, int a, long *src
         case OR_FACE_OUTFLOW:
             outflow = 1;
             break;
+        case OR_FACE_NODAL:
+            nodal = 1;
+            if (face == 3)
+                lid = m->lid_on;
+            break;
         case OR_FACE_SYMMETRY:
             up[k] = c[k];
             e[k] = -e[k];
@@ -409,7 +433,7 @@ static int resolve_link(const or_model *m, int x, int y, int z, int a, long *src
         }
     }
     *term = 0.0;
-    if (bounce) {
+    if (bounce || nodal) {
         double U[3] = {0.0, 0.0, 0.0};
         if (inlet)
             inlet_velocity(m, x, y, z, U);
@@ -420,7 +444,18 @@ static int resolve_link(const or_model *m, int x, int y, int z, int a, long *src
         *term = 2.0 * v->t[a] * m->rho0 * eU * INV_CS2;
         *src = node_index(m, x, y, z);
         *slot = v->opp[a];
-        return OR_LINK_WALL;
+        if (bounce)
+            return OR_LINK_WALL;
+        if (!nested) { /* nodal: the opposite population that has just arrived */
+            long s2;
+            int sl2;
+            double t2;
+            if (resolve_link_at(m, x, y, z, v->opp[a], &s2, &sl2, &t2, 1) == OR_LINK_STREAM) {
+                *src = s2;
+                *slot = sl2;
+            }
+        }
+        return OR_LINK_NODAL;
     }
     if (outflow) {
         *src = node_index(m, x, y, z);
@@ -609,7 +644,7 @@ static int setup_model(or_model *m, int lattice, int nx, int ny, int nz, double 
         return OR_ERR_ARG;
     int ninlet = 0;
     for (int i = 0; i < 6; ++i) {
-        if (faces[i] < OR_FACE_PERIODIC || faces[i] > OR_FACE_SYMMETRY)
+        if (faces[i] < OR_FACE_PERIODIC || faces[i] > OR_FACE_NODAL)
             return OR_ERR_ARG;
         /* periodic faces come in pairs */
         if ((faces[i] == OR_FACE_PERIODIC) != (faces[i ^ 1] == OR_FACE_PERIODIC))
@@ -626,7 +661,7 @@ static int setup_model(or_model *m, int lattice, int nx, int ny, int nz, double 
     m->N = (long)nx * ny * nz;
     for (int k = 0; k < 3; ++k)
         m->periodic[k] = m->face[2 * k] == OR_FACE_PERIODIC;
-    m->lid_on = m->face[3] == OR_FACE_WALL;
+    m->lid_on = m->face[3] == OR_FACE_WALL || m->face[3] == OR_FACE_NODAL;
     for (int k = 0; k < 3; ++k)
         m->lid[k] = lid ? lid[k] : 0.0;
     m->omega = 1.0 / tau;

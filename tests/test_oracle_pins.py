@@ -540,3 +540,67 @@ def test_inflow_outflow_channel_develops_poiseuille():
     slope = (P[:, 40] - P[:, 80]).mean() / 40
     assert abs(slope / (8 * nu * umax / ny ** 2) - 1) < 0.02
     assert abs(P[:, -1].mean() - 0.33) < 0.01 * (P[:, 0].mean() - 0.33)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.2: the paper's modified nodal bounce-back (walls on the nodes)
+
+NODAL_CHANNEL = ["periodic", "periodic", "nodal", "nodal", "periodic", "periodic"]
+
+
+@pytest.mark.parametrize("lattice", ["d2q9", "d3q19", "d3q27"])
+def test_nodal_couette_walls_on_the_nodes(lattice):
+    """Moving top wall: the linear profile U y/(ny - 1) with u = 0 on the
+    bottom row of nodes and u = U on the top row, for any tau (half-way
+    bounce-back puts the walls half a link out instead)."""
+    ny, U = 12, 0.02
+    y = np.arange(ny)
+    for tau in (0.6, 1.3):
+        nu = W.viscosity(tau)
+        _, u = oracle.run(lattice, 1, ny, 1, tau, NODAL_CHANNEL, int(30 * ny * ny / nu),
+                          lid=[U, 0, 0])
+        assert np.abs(u[0] - U * y / (ny - 1)).max() < 1e-10 * U
+        assert np.abs(u[1:]).max() < 1e-12 * U
+
+
+@pytest.mark.parametrize("lattice", ["d2q9", "d3q19"])
+def test_nodal_poiseuille(lattice):
+    """Body-force channel between nodal walls: exact second differences -G/nu
+    and a parabola through the wall nodes up to a constant slip that depends
+    on tau (as for BGK half-way bounce-back, but a different slip)."""
+    ny, G = 14, 1e-6
+    Q, d = oracle.dims(lattice)
+    y = np.arange(ny)
+    slips = []
+    for tau in (0.6, 0.8, 1.2):
+        nu = W.viscosity(tau)
+        F = np.zeros((d, ny))
+        F[0] = G
+        _, u = oracle.run(lattice, 1, ny, 1, tau, NODAL_CHANNEL, int(30 * ny * ny / nu), F=F)
+        ux = u[0]
+        d2 = ux[2:] - 2 * ux[1:-1] + ux[:-2]
+        assert np.abs(d2 * nu / G + 1).max() < 1e-8
+        par = G / (2 * nu) * y * (ny - 1 - y)
+        slip = ux - par
+        assert np.abs(slip - slip.mean()).max() < 1e-9 * par.max()
+        slips.append(slip.mean() / par.max())
+        _, uh = oracle.run(lattice, 1, ny, 1, tau, "channel", int(30 * ny * ny / nu), F=F)
+        assert np.abs(uh[0] - ux).max() > 1e-3 * par.max()  # not half-way bounce-back
+    assert 0 < slips[0] < slips[1] < slips[2] < 0.05
+
+
+def test_nodal_wall_with_symmetry_equals_mirrored_channel():
+    """A nodal wall below and a symmetry face above give the lower half of the
+    nodal channel of twice the height (mirror plane half a link above)."""
+    nx, m, nz = 7, 6, 5
+    ny = 2 * m
+    p0h, u0h = W.random_smooth_state(nx, m, nz, 3, amp_u=0.03, seed=6)
+    p0h = p0h.reshape(nz, m, nx)
+    u0h = u0h.reshape(3, nz, m, nx)
+    p0 = np.concatenate([p0h, p0h[:, ::-1]], axis=1).ravel()
+    u0 = np.concatenate([u0h, u0h[:, :, ::-1]], axis=2)
+    u0[1, :, m:] *= -1
+    _, uf = oracle.run("d3q19", nx, ny, nz, 0.7, NODAL_CHANNEL, 25, p0=p0, u0=u0.reshape(3, -1))
+    half = ["periodic", "periodic", "nodal", "symmetry", "periodic", "periodic"]
+    _, uh = oracle.run("d3q19", nx, m, nz, 0.7, half, 25, p0=p0h.ravel(), u0=u0h.reshape(3, -1))
+    assert np.abs(uf.reshape(3, nz, ny, nx)[:, :, :m].reshape(3, -1) - uh).max() < 1e-15
