@@ -88,9 +88,16 @@ typedef enum {
  *                      convective outflow without printing it; behind a
  *                      velocity inlet an outlet must fix the pressure level);
  *   LBM_FACE_SYMMETRY  specular reflection (free slip): the coordinate stays
- *                      that of x and the direction's normal component flips.
+ *                      that of x and the direction's normal component flips;
+ *   LBM_FACE_NODAL     the paper's "second-order modified nodal bounce back"
+ *                      (Sec. 2.2, Eq. (bb)): the wall lies ON the boundary
+ *                      nodes, which collide like the bulk; a population
+ *                      entering one from outside is the opposite one that has
+ *                      just arrived from inside, f_a(x) = f_abar(x) (plus the
+ *                      lid term on +y; the node's own f*_abar(x) where that
+ *                      one also comes from outside, as at corners).
  * A link crossing a wall or inlet bounces whatever else it crosses; then
- * outflow wins over symmetry and periodic.  The inlet term wins over the lid
+ * nodal, then outflow win over symmetry and periodic.  The inlet term wins over the lid
  * term on a link crossing both.  Faces are ordered -x, +x, -y, +y, -z, +z;
  * D2Q9 ignores the z faces. */
 typedef enum {
@@ -98,7 +105,8 @@ typedef enum {
     LBM_FACE_WALL = 1,
     LBM_FACE_INLET = 2,
     LBM_FACE_OUTFLOW = 3,
-    LBM_FACE_SYMMETRY = 4
+    LBM_FACE_SYMMETRY = 4,
+    LBM_FACE_NODAL = 5
 } lbm_face;
 
 /* Storage of the distributions in HBM.  Arithmetic is FP64 for LBM_F64 and

@@ -87,7 +87,7 @@ bool resolve_faces(int lattice, int bc, const lbm_opts &o, int face[6])
         face[4] = face[5] = LBM_FACE_PERIODIC;
     int ninlet = 0;
     for (int i = 0; i < 6; ++i) {
-        if (face[i] < LBM_FACE_PERIODIC || face[i] > LBM_FACE_SYMMETRY)
+        if (face[i] < LBM_FACE_PERIODIC || face[i] > LBM_FACE_NODAL)
             return false;
         if ((face[i] == LBM_FACE_PERIODIC) != (face[i ^ 1] == LBM_FACE_PERIODIC))
             return false;
@@ -194,9 +194,9 @@ void fill_params(lbm_ctx *c)
     p.open_faces = 0;
     for (int i = 0; i < 6; ++i)
         if (c->face[i] == LBM_FACE_INLET || c->face[i] == LBM_FACE_OUTFLOW ||
-            c->face[i] == LBM_FACE_SYMMETRY)
+            c->face[i] == LBM_FACE_SYMMETRY || c->face[i] == LBM_FACE_NODAL)
             p.open_faces |= 1 << i;
-    p.lid_on = c->face[3] == LBM_FACE_WALL;
+    p.lid_on = c->face[3] == LBM_FACE_WALL || c->face[3] == LBM_FACE_NODAL;
     p.inlet_face = -1;
     for (int i = 0; i < 6; ++i) {
         p.face[i] = c->face[i];

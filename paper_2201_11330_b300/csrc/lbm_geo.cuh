@@ -16,9 +16,15 @@
 //              half of the equilibrium, u(x) from the node's own
 //              post-collision populations;
 //   symmetry   the coordinate stays that of x and the direction's component
-//              normal to the face is reflected (specular, free slip).
-// A wall or inlet crossing wins over an outflow crossing, which wins over
-// the rest.  If the node so found is solid (bit a of the node's link word),
+//              normal to the face is reflected (specular, free slip);
+//   nodal      the paper's modified nodal bounce-back (Sec. 2.2, Eq. (bb)):
+//              the wall lies on the boundary nodes, which collide like the
+//              bulk; f_a(x) = f_abar(x) after propagation, the opposite
+//              population that has just arrived from inside (plus the lid
+//              term on +y; the node's own f*_abar(x) where that one comes
+//              from outside too, as at corners).
+// A wall or inlet crossing wins over a nodal one, then outflow, then the
+// rest.  If the node so found is solid (bit a of the node's link word),
 // the population bounces back at x, and the link's momentum exchange
 // 2 f*_abar(x) e_abar counts towards the force on the obstacle (Sec. 5).
 // Solid nodes (bit 31) are not updated.
@@ -29,7 +35,14 @@
 namespace lbm {
 
 // lbm_face of include/lbm.h
-enum FaceType { F_PERIODIC = 0, F_WALL = 1, F_INLET = 2, F_OUTFLOW = 3, F_SYMMETRY = 4 };
+enum FaceType {
+    F_PERIODIC = 0,
+    F_WALL = 1,
+    F_INLET = 2,
+    F_OUTFLOW = 3,
+    F_SYMMETRY = 4,
+    F_NODAL = 5
+};
 
 // What a link crossing one side of one axis does; OR-ed over the components
 // of a direction.
@@ -39,6 +52,7 @@ enum SideKind : unsigned {
     SK_INLET = 4u,   // with the inlet velocity's term
     SK_OUT = 8u,     // pressure outlet
     SK_SYM = 16u,    // symmetry plane
+    SK_NODAL = 32u,  // nodal bounce-back (with SK_LID on the +y face)
 };
 constexpr unsigned kSolidBit = 1u << 31;
 
@@ -58,6 +72,8 @@ __device__ __forceinline__ unsigned side_kind(int type, bool lid)
         return SK_OUT;
     case F_SYMMETRY:
         return SK_SYM;
+    case F_NODAL:
+        return SK_NODAL | (lid ? SK_LID : 0u);
     default:
         return 0u;
     }
@@ -205,7 +221,7 @@ __device__ __forceinline__ void geo_node(const typename Sto<S>::T *src, typename
         int off, slot;
         unsigned kind;
         link_of<L, a>(X, Y, Z, off, kind, slot);
-        const bool own = (kind & (SK_BOUNCE | SK_OUT)) || ((lw >> a) & 1u);
+        const bool own = (kind & (SK_BOUNCE | SK_OUT | SK_NODAL)) || ((lw >> a) & 1u);
         raw[a] = ld(own ? src + b * N + n : src + (size_t)slot * N + (n + off));
     });
     R g[Q];
@@ -224,6 +240,9 @@ __device__ __forceinline__ void geo_node(const typename Sto<S>::T *src, typename
             } else if (kind & SK_LID) {
                 v = o_add(v, c.lid[a]);
             }
+        } else if (kind & SK_NODAL) {
+            // fallback f*_abar(x); replaced below where the opposite
+            // population streamed in
         } else if (kind & SK_OUT) {
             const R eu = R(ex) * ub[0] + R(ey) * ub[1] + R(ez) * ub[2];
             const R q = o_fma(o_mul(R(4.5), eu), eu, o_mul(R(-1.5), ubb));
@@ -242,6 +261,24 @@ __device__ __forceinline__ void geo_node(const typename Sto<S>::T *src, typename
         }
         g[a] = v;
     });
+    if (any & SK_NODAL) {
+        SFor<0, Q>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            constexpr int b = opp<L>(a);
+            int off, slot, offb, slotb;
+            unsigned kind, kindb;
+            link_of<L, a>(X, Y, Z, off, kind, slot);
+            if ((kind & (SK_BOUNCE | SK_NODAL)) != SK_NODAL)
+                return;
+            link_of<L, b>(X, Y, Z, offb, kindb, slotb);
+            const bool streamed =
+                !(kindb & (SK_BOUNCE | SK_OUT | SK_NODAL)) && !((lw >> b) & 1u);
+            R v = streamed ? g[b] : g[a];
+            if (kind & SK_LID)
+                v = o_add(v, c.lid[a]);
+            g[a] = v;
+        });
+    }
     R u[3], s_, rho_;
     collide<L, R, MODEL, FORCE>(g, F, c, u, s_, rho_);
     if constexpr (MON == 1)
@@ -338,7 +375,7 @@ __global__ void __launch_bounds__(256) k_links(const unsigned char *solid, unsig
             int off, slot;
             unsigned kind;
             link_of<L, a>(X, Y, Z, off, kind, slot);
-            if (!(kind & (SK_BOUNCE | SK_OUT)) && solid[n + off])
+            if (!(kind & (SK_BOUNCE | SK_OUT | SK_NODAL)) && solid[n + off])
                 w |= 1u << a;
         });
     }

@@ -66,7 +66,7 @@ struct StepParams {
     const int *nlist;       // general kernel on a node list: the nodes, or NULL (full grid)
     int nlist_len;          // entries of nlist
     long long part_base;    // node-list launches: first partial entry of their blocks
-    int open_faces;         // bit f: face f is an inlet, outflow or symmetry face
+    int open_faces;         // bit f: face f is an inlet, outflow, symmetry or nodal face
     double *partials;  // per-block monitor sums (RED kernels)
     const float *F;  // body force, d*N component-major (FORCE kernels)
     void *u_out;     // velocity output, d*N component-major, kernel arithmetic type (UOUT)
@@ -576,8 +576,8 @@ __global__ void __launch_bounds__(256, 5) k_step_gather_red(const typename Sto<S
 }
 
 // A node the plain kernel cannot update in a box with per-face boundaries or
-// obstacles: solid, with an obstacle link, or on an inlet, outflow or
-// symmetry face.
+// obstacles: solid, with an obstacle link, or on an inlet, outflow, symmetry
+// or nodal face.
 __device__ __forceinline__ bool needs_general(const StepParams &p, int n, int x, int y, int z)
 {
     const int f = p.open_faces;

@@ -22,9 +22,10 @@ LIB_PATH = os.path.join(HERE, "liblbm.so")
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_STATE, LBM_ERR_NOMEM = 0, -1, -2, -3, -4, -5
 LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 = 0, 1, 2
 LBM_BC_PERIODIC, LBM_BC_CAVITY, LBM_BC_CHANNEL, LBM_BC_FACES = 0, 1, 2, 3
-LBM_FACE_PERIODIC, LBM_FACE_WALL, LBM_FACE_INLET, LBM_FACE_OUTFLOW, LBM_FACE_SYMMETRY = 0, 1, 2, 3, 4
+LBM_FACE_PERIODIC, LBM_FACE_WALL, LBM_FACE_INLET, LBM_FACE_OUTFLOW = 0, 1, 2, 3
+LBM_FACE_SYMMETRY, LBM_FACE_NODAL = 4, 5
 FACES = {"periodic": LBM_FACE_PERIODIC, "wall": LBM_FACE_WALL, "inlet": LBM_FACE_INLET,
-         "outflow": LBM_FACE_OUTFLOW, "symmetry": LBM_FACE_SYMMETRY}
+         "outflow": LBM_FACE_OUTFLOW, "symmetry": LBM_FACE_SYMMETRY, "nodal": LBM_FACE_NODAL}
 LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = 0, 1, 2, 3
 LBM_COLL_BGK, LBM_COLL_TRT = 0, 1
 LBM_KERNEL_AUTO, LBM_KERNEL_PLAIN, LBM_KERNEL_STAGED, LBM_KERNEL_PAIRED = 0, 1, 2, 3
@@ -285,7 +286,8 @@ class Lattice:
     (d, N) in FP32.  Calls launch on torch's current stream.
 
     ``bc`` is "periodic", "cavity", "channel" or six face types ("periodic",
-    "wall", "inlet", "outflow", "symmetry"; order -x, +x, -y, +y, -z, +z).
+    "wall", "inlet", "outflow", "symmetry", "nodal"; order -x, +x, -y, +y,
+    -z, +z).
     ``obstacles=True`` reserves the link words for ``set_geometry``.
     """
 

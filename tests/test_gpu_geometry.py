@@ -288,3 +288,48 @@ def test_sphere_512x128x128_matches_oracle_at_point_a():
     assert abs(got[0][a] - ref[0][a]) < 1e-15
     assert np.abs(got[1][:, a] - U * np.array([1, 0, 0])).max() > 1e-6  # A sees the sphere
     assert np.abs(got[2] - ref[2]).max() < 1e-12 * np.abs(ref[2]).max()
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("lattice,shape,faces,obst", [
+    ("d3q19", (29, 23, 17), ["nodal"] * 6, True),
+    ("d3q27", (25, 19, 14), ["inlet", "outflow", "nodal", "nodal", "symmetry", "nodal"], True),
+    ("d2q9", (61, 37, 1), ["nodal", "nodal", "nodal", "nodal", "periodic", "periodic"], False),
+])
+def test_nodal_bounce_back_parity(lattice, shape, faces, obst, storage):
+    """The paper's nodal bounce-back faces (with a lid on +y, obstacles
+    touching nodal faces, an inlet and an outflow) against the oracle."""
+    Q, d = oracle.dims(lattice)
+    nx, ny, nz = shape
+    p0, u0 = W.random_smooth_state(nx, ny, nz, d, amp_u=0.03, amp_p=2e-3, seed=33)
+    sol = None
+    if obst:
+        sol = np.zeros((nz, ny, nx), np.uint8)
+        sol[2:6, 0:3, 8:12] = 1
+        sol[nz // 2:nz // 2 + 3, 9:12, 0:4] = 1
+        u0[:, sol.ravel() != 0] = 0
+    inl = None
+    if "inlet" in faces:
+        inl = np.zeros((d, ny * nz))
+        inl[0] = 0.03
+    F = W.fourier_force(nx, ny, nz, amplitude=2e-5, seed=13, dims=d)
+    got, ref = run_pair(lattice, shape, 0.63, faces, 45, storage=storage, solid=sol, inlet=inl,
+                        lid=(0.06, 0.0, 0.01), F=F, p0=p0, u0=u0, force_out=obst)
+    eu, ep = field_errors(got, ref, 0.05)
+    assert eu < TOL_U[storage] and ep < 10 * TOL_U[storage], (eu, ep)
+    if obst:
+        assert np.abs(got[2] - ref[2]).max() < (1e-12 if storage == "f64" else 1e-4) * \
+            np.abs(ref[2]).max()
+
+
+def test_nodal_couette_on_gpu():
+    """Nodal walls put the Couette profile's ends on the wall nodes (FP64)."""
+    from paper_2201_11330_b300.lbm import Lattice
+    ny, U, tau = 12, 0.02, 1.3
+    nu = W.viscosity(tau)
+    lat = Lattice("d3q19", 1, ny, 1, tau, ["periodic", "periodic", "nodal", "nodal", "periodic",
+                                           "periodic"], storage="f64", lid=(U, 0, 0))
+    lat.init()
+    lat.step(int(30 * ny * ny / nu))
+    _, u = lat.macroscopic()
+    assert np.abs(u[0].cpu().numpy() - U * np.arange(ny) / (ny - 1)).max() < 1e-10 * U
