@@ -68,6 +68,10 @@ inline cudaError_t with_model(int m, F &&f)
     }
 }
 
+// plain D3Q27 pull / gather kernels with 16-bit storage: the four-block bound
+template <class L, int S>
+constexpr bool kOcc4 = L::Q == 27 && (S == ST_F16S || S == ST_BF16S);
+
 template <class L, int S>
 cudaError_t launch_storage(const Launch &l)
 {
@@ -171,8 +175,14 @@ cudaError_t launch_storage(const Launch &l)
             return with_model(l.model, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
                     return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
-                        k_step<L, S, PAT_PULL, decltype(C)::value, decltype(Fo)::value, false,
-                               decltype(Rd)::value><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                        constexpr int c = decltype(C)::value;
+                        constexpr bool fo = decltype(Fo)::value, rd = decltype(Rd)::value;
+                        if constexpr (kOcc4<L, S> && !rd)
+                            k_step_occ4<L, S, PAT_PULL, c, fo>
+                                <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                        else
+                            k_step<L, S, PAT_PULL, c, fo, false, rd>
+                                <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
                         return cudaGetLastError();
                     });
                 });
@@ -181,12 +191,17 @@ cudaError_t launch_storage(const Launch &l)
         if (l.pattern == PAT_GATHER) {
             return with_model(l.model, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
+                    constexpr int c = decltype(C)::value;
+                    constexpr bool fo = decltype(Fo)::value;
                     if (l.sp.partials != nullptr)
-                        k_step_gather_red<L, S, decltype(C)::value, decltype(Fo)::value>
-                            <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                        k_step_gather_red<L, S, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, dst,
+                                                                                         l.sp);
+                    else if constexpr (kOcc4<L, S>)
+                        k_step_occ4<L, S, PAT_GATHER, c, fo><<<l.grid, l.block, 0, l.stream>>>(
+                            src, dst, l.sp);
                     else
-                        k_step<L, S, PAT_GATHER, decltype(C)::value, decltype(Fo)::value, false,
-                               false><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                        k_step<L, S, PAT_GATHER, c, fo, false, false>
+                            <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
                     return cudaGetLastError();
                 });
             });
