@@ -166,8 +166,10 @@ size_t lbm_workspace_bytes(int lattice, int nx, int ny, int nz, const lbm_opts *
  * tau <= 1/2, rho0 <= 0, N >= 2^31, misaligned workspace; with LBM_BC_FACES
  * or opts.geometry: an unpaired periodic face, more than one inlet, or the
  * AA scheme, which supports the three named box types only), LBM_ERR_NOMEM
- * (workspace too small).  LBM_BC_FACES and obstacles run the general step
- * kernel (pull scheme, one node per thread). */
+ * (workspace too small).  LBM_BC_FACES and obstacles run the pull scheme:
+ * the plain (16-bit storage: paired) kernel on the nodes that touch only
+ * walls, the lid and periodic faces, and the general kernel, one node per
+ * thread, on a list of the rest; the staged variant is not available. */
 int lbm_create(int lattice, int nx, int ny, int nz, double tau, int bc, const lbm_opts *opts,
                void *dev_workspace, size_t bytes, void *cuda_stream, lbm_ctx **out);
 

@@ -311,6 +311,8 @@ int build_node_list(lbm_ctx *c)
     Launch l = base_launch(c, K_FLAGS);
     l.storage = LBM_F32;  // the flag kernel is instantiated once per lattice
     l.flags = c->nflags;
+    l.pair = use_pair(c, PAT_PULL);  // the paired kernel updates whole pairs
+    c->list_pairs = l.pair;
     if (dispatch(c->lattice, l) != cudaSuccess)
         return LBM_ERR_CUDA;
     std::vector<unsigned char> flags(N);
@@ -344,9 +346,10 @@ int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u
     if (reduce_blocks)
         l.sp.partials = c->step_partials;
     if (c->geo) {
-        // pull scheme, one node per thread: the plain kernel on every node
-        // it can update (walls, lid, periodic faces; same arithmetic, bitwise
-        // equal results), the general kernel on the listed rest
+        // pull scheme: the plain kernel (two nodes per thread for 16-bit
+        // storage) on every node it can update (walls, lid, periodic faces;
+        // same arithmetic, bitwise equal results), the general kernel, one
+        // node per thread, on the listed rest
         const int mon = reduce_blocks ? (obstacle_force ? 2 : 1) : 0;
         const long long grid_blocks = (long long)l.grid.x * l.grid.y * l.grid.z;
         if (!c->nflags) {
@@ -356,11 +359,20 @@ int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u
                 *reduce_blocks = grid_blocks;
             return dispatch(c->lattice, l) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
         }
-        if (!c->list_ready) {
+        if (!c->list_ready || c->list_pairs != use_pair(c, PAT_PULL)) {
             const int rc = build_node_list(c);
             if (rc != LBM_OK)
                 return rc;
         }
+        // the plain (or paired) kernel on the nodes it can update; its
+        // reduction partials come first, the general kernel's after them
+        Launch ls = l;
+        ls.skip = true;
+        ls.mon = mon;
+        ls.pair = c->list_pairs;
+        if (ls.pair)
+            ls.grid = dim3((c->nx + 2 * kPairThreads - 1) / (2 * kPairThreads), c->ny, c->nz);
+        const long long skip_blocks = (long long)ls.grid.x * ls.grid.y * ls.grid.z;
         const long long gblocks = (c->n_general + 255) / 256;
         if (gblocks > 0) {
             Launch lg = l;
@@ -368,19 +380,16 @@ int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u
             lg.mon = mon;
             lg.sp.nlist = c->nlist;
             lg.sp.nlist_len = (int)c->n_general;
-            lg.sp.part_base = grid_blocks;
+            lg.sp.part_base = skip_blocks;
             lg.grid = dim3((unsigned)gblocks, 1, 1);
             lg.block = dim3(256, 1, 1);
             if (dispatch(c->lattice, lg) != cudaSuccess)
                 return LBM_ERR_CUDA;
         }
-        Launch ls = l;
-        ls.skip = true;
-        ls.mon = mon;
         if (dispatch(c->lattice, ls) != cudaSuccess)
             return LBM_ERR_CUDA;
         if (reduce_blocks)
-            *reduce_blocks = grid_blocks + gblocks;
+            *reduce_blocks = skip_blocks + gblocks;
         return LBM_OK;
     }
     if (u_out) {
@@ -673,7 +682,7 @@ int lbm_set_kernel_variant(lbm_ctx *c, int variant)
         return LBM_ERR_ARG;
     if (variant == LBM_KERNEL_PAIRED && !pair_eligible(c))
         return LBM_ERR_ARG;
-    if (c->geo && variant != LBM_KERNEL_AUTO && variant != LBM_KERNEL_PLAIN)
+    if (c->geo && variant == LBM_KERNEL_STAGED)
         return LBM_ERR_ARG;
     c->kernel_variant = variant;
     return LBM_OK;
@@ -684,7 +693,7 @@ int lbm_kernel_variant_in_use(const lbm_ctx *c)
     if (!c)
         return LBM_ERR_ARG;
     if (c->geo)
-        return LBM_KERNEL_PLAIN;
+        return use_pair(c) ? LBM_KERNEL_PAIRED : LBM_KERNEL_PLAIN;
     return use_pair(c) ? LBM_KERNEL_PAIRED : use_bulk(c) ? LBM_KERNEL_STAGED : LBM_KERNEL_PLAIN;
 }
 

@@ -44,6 +44,7 @@ struct lbm_ctx {
     unsigned char *nflags;      // per-node "needs the general kernel" flags (workspace)
     int *nlist;                 // the nodes that need the general kernel (workspace)
     bool list_ready;
+    bool list_pairs;            // the list was built for the paired kernel
     long long n_general;        // entries of nlist
     lbm::StepParams sp;
     // adjoint run recorded by lbm_adjoint_forward for lbm_adjoint_backward

@@ -338,16 +338,19 @@ __global__ void __launch_bounds__(256) k_step_geo(const typename Sto<S>::T *src,
     }
 }
 
-// flags[n] = 1 for the nodes the plain kernel cannot update (needs_general).
+// flags[n] = 1 for the nodes the plain kernel cannot update (needs_general);
+// with `pairs` (nx even, the paired kernel) both nodes of such a pair.
 template <class L>
-__global__ void __launch_bounds__(256) k_node_flags(unsigned char *flags, const StepParams p)
+__global__ void __launch_bounds__(256) k_node_flags(unsigned char *flags, const StepParams p,
+                                                    bool pairs)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= p.nx)
         return;
     const int n = x + p.nx * (y + p.ny * z);
-    flags[n] = needs_general(p, n, x, y, z) ? 1 : 0;
+    const bool g = needs_general(p, n, x, y, z) || (pairs && needs_general(p, n ^ 1, x ^ 1, y, z));
+    flags[n] = g ? 1 : 0;
 }
 
 // Link words from a solid mask: bit 31 = the node is solid; bit a = the

@@ -78,7 +78,7 @@ cudaError_t launch_storage(const Launch &l)
     using T = typename Sto<S>::T;
     const T *src = (const T *)l.src;
     T *dst = (T *)l.dst;
-    if (l.kind == K_STEP && l.pair) {
+    if (l.kind == K_STEP && l.pair && !l.skip) {
         if constexpr (S == ST_F16S || S == ST_BF16S) {
             const dim3 grid((l.sp.nx + 2 * kPairThreads - 1) / (2 * kPairThreads), l.sp.ny, l.sp.nz);
             return with_model(l.model, [&](auto C) {
@@ -123,6 +123,22 @@ cudaError_t launch_storage(const Launch &l)
             return with_bool(l.force, [&](auto Fo) {
                 constexpr int c = decltype(C)::value;
                 constexpr bool fo = decltype(Fo)::value;
+                if constexpr (S == ST_F16S || S == ST_BF16S) {
+                    if (l.pair) {
+                        const auto *s16 = (const unsigned short *)l.src;
+                        auto *d16 = (unsigned short *)l.dst;
+                        if (l.mon == 1)
+                            k_step_pair_skip<L, S, c, fo, 1>
+                                <<<l.grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                        else if (l.mon == 2)
+                            k_step_pair_skip<L, S, c, fo, 2>
+                                <<<l.grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                        else
+                            k_step_pair_skip<L, S, c, fo, 0>
+                                <<<l.grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                        return cudaGetLastError();
+                    }
+                }
                 if (l.mon == 1)
                     k_step_skip<L, S, c, fo, 1><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
                 else if (l.mon == 2)
@@ -135,7 +151,7 @@ cudaError_t launch_storage(const Launch &l)
     }
     if (l.kind == K_FLAGS) {
         if constexpr (S == ST_F32) {  // storage-independent: one instantiation per lattice
-            k_node_flags<L><<<l.grid, l.block, 0, l.stream>>>(l.flags, l.sp);
+            k_node_flags<L><<<l.grid, l.block, 0, l.stream>>>(l.flags, l.sp, l.pair);
             return cudaGetLastError();
         } else {
             return cudaErrorInvalidValue;

@@ -259,7 +259,10 @@ __device__ __forceinline__ int shifted_row(const StepParams &p, int y, int z, bo
     return ys + p.ny * zs;
 }
 
-template <class L, int S, int PAT, int MODEL, bool FORCE, bool IROW, bool RED>
+// SKIP (pull scheme only): a box with per-face boundaries or obstacles; pairs
+// with a node that needs the general kernel are loaded (their words feed the
+// neighbour lanes' realignment) but neither collided nor stored.
+template <class L, int S, int PAT, int MODEL, bool FORCE, bool IROW, bool RED, bool SKIP = false>
 __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned short *dst,
                                           const StepParams &p)
 {
@@ -276,6 +279,12 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
     const size_t n = (size_t)row * nx + x;  // even
     const bool xper = p.periodic & 1;
     const bool top = p.lid_on && (y == p.ny - 1);
+    bool own = active;  // this pair is collided and stored here
+    if constexpr (SKIP) {
+        static_assert(PAT == PAT_PULL, "the pull scheme only");
+        if (active)
+            own = !needs_general(p, (int)n, x, y, z) && !needs_general(p, (int)n + 1, x + 1, y, z);
+    }
 
     auto word = [&](const unsigned short *base, size_t i) -> unsigned {
         return *reinterpret_cast<const unsigned *>(base + i);
@@ -355,7 +364,7 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
 
     float mon[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     // ---- collide nodes x and x+1 together (packed FP32) ------------------------
-    if (active) {
+    if (own) {
         float2 g[Q];
         SFor<0, Q>::run([&](auto A_) {
             constexpr int a = decltype(A_)::value;
@@ -396,7 +405,7 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
         constexpr int ex = L::e(a, 0);
         const unsigned O = W[a];
         if constexpr (PAT == PAT_PULL) {
-            if (active)
+            if (own)
                 put_word((size_t)a * N + n, O);
             return;
         }
@@ -455,6 +464,26 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
     });
     if constexpr (RED)
         block_monitor(mon, p.partials, grid_block_index());
+}
+
+// The pull step of a box with per-face boundaries or obstacles on the pairs
+// the paired kernel can update (see k_step_skip).  MON: 0, 1 = monitor sums,
+// 2 = obstacle force (zero here).
+template <class L, int S, int MODEL, bool FORCE, int MON>
+__global__ void __launch_bounds__(kPairThreads) k_step_pair_skip(const unsigned short *src,
+                                                                 unsigned short *dst,
+                                                                 const StepParams p)
+{
+    if constexpr (MON == 2) {
+        if (threadIdx.x < kReduceVals)
+            p.partials[grid_block_index() * kPartialStride + threadIdx.x] = 0.0;
+    }
+    const int y = blockIdx.y, z = blockIdx.z;
+    const bool irow = y > 0 && y < p.ny - 1 && (L::D == 2 || (z > 0 && z < p.nz - 1));
+    if (irow)
+        pair_body<L, S, PAT_PULL, MODEL, FORCE, true, MON == 1, true>(src, dst, p);
+    else
+        pair_body<L, S, PAT_PULL, MODEL, FORCE, false, MON == 1, true>(src, dst, p);
 }
 
 template <class L, int S, int PAT, int MODEL, bool FORCE, bool RED = false>
