@@ -222,6 +222,17 @@ int lbm_step_force(lbm_ctx *ctx, int64_t n, double *out);
  * launch per step. */
 int lbm_step(lbm_ctx *ctx, int64_t n);
 
+/* CUDA graphs for lbm_step: with steps = G (even, >= 2) lbm_step(n) for
+ * n >= 2G runs its launches as replays of a G-step graph (captured once on a
+ * private stream the context creates, replayed into the context's stream,
+ * re-captured after any change of the launch parameters); the results are
+ * those of direct launches, bit for bit.  Pays where a step's kernels are
+ * shorter than their launch overhead.  steps = 0: direct launches only;
+ * -1 (the default): G = 32 for states up to 256 MB, else direct.  Never used
+ * while the context's stream is itself being captured.  LBM_ERR_ARG for
+ * other values. */
+int lbm_set_graph_steps(lbm_ctx *ctx, int steps);
+
 /* Steps taken since lbm_init (or the value given to lbm_set_state). */
 int64_t lbm_step_count(const lbm_ctx *ctx);
 

@@ -179,6 +179,7 @@ void fill_lid_terms(lbm_ctx *c)
 
 void fill_params(lbm_ctx *c)
 {
+    ++c->param_version;
     StepParams &p = c->sp;
     p.nx = c->nx;
     p.ny = c->ny;
@@ -331,6 +332,7 @@ int build_node_list(lbm_ctx *c)
         return LBM_ERR_CUDA;
     c->n_general = (long long)list.size();
     c->list_ready = true;
+    ++c->param_version;  // the general kernel's grid changed
     return LBM_OK;
 }
 
@@ -549,6 +551,7 @@ int lbm_create(int lattice, int nx, int ny, int nz, double tau, int bc, const lb
     c->nflags = wants_node_list(o) ? (unsigned char *)(c->ws + L.flags_off) : nullptr;
     c->nlist = wants_node_list(o) ? (int *)(c->ws + L.nlist_off) : nullptr;
     c->list_ready = false;
+    c->graph_mode = -1;  // automatic; graphs and their stream are made on first use
     fill_params(c);
     c->sp.inlet = nullptr;
     *out = c;
@@ -584,6 +587,8 @@ int lbm_init(lbm_ctx *c, const double *p, const double *u)
 
 int lbm_set_force(lbm_ctx *c, const float *force)
 {
+    if (c)
+        ++c->param_version;
     if (!c)
         return LBM_ERR_ARG;
     if (!c->opts.has_force)
@@ -635,6 +640,7 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *solid)
     c->links_ready = true;
     c->sp.links = c->links;
     c->list_ready = false;  // the general kernel's nodes change with the obstacles
+    ++c->param_version;
     c->initialized = false;
     return LBM_OK;
 }
@@ -646,6 +652,101 @@ int lbm_set_inlet(lbm_ctx *c, const float *u_in)
     if (c->sp.inlet_face < 0)
         return LBM_ERR_STATE;
     keep_inlet(c, u_in);
+    ++c->param_version;
+    return LBM_OK;
+}
+
+namespace {
+
+// The launches of time step `step` with the pull lattices in `cur`.
+int launch_one_step(lbm_ctx *c, int64_t step, int cur)
+{
+    if (c->opts.aa) {
+        const int pat = (step % 2 == 0) ? PAT_GATHER : PAT_LOCAL;
+        return ctx_launch_step(c, c->f[0], c->f[0], pat, nullptr);
+    }
+    return ctx_launch_step(c, c->f[cur], c->f[1 - cur], PAT_PULL, nullptr);
+}
+
+int step_direct(lbm_ctx *c, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        const int rc = launch_one_step(c, c->step, c->cur);
+        if (rc != LBM_OK)
+            return rc;
+        if (!c->opts.aa)
+            c->cur = 1 - c->cur;
+        ++c->step;
+    }
+    return LBM_OK;
+}
+
+// Steps per graph: graphs pay where a step's kernels are shorter than their
+// launches (the automatic choice: states up to 256 MB).
+int graph_steps(const lbm_ctx *c)
+{
+    if (c->graph_mode >= 0)
+        return c->graph_mode;
+    return c->state_bytes <= ((size_t)256 << 20) ? 32 : 0;
+}
+
+void drop_graphs(lbm_ctx *c)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (c->graph[k])
+            cudaGraphExecDestroy(c->graph[k]);
+        c->graph[k] = nullptr;
+    }
+}
+
+// Captures G steps starting from the context's current step and lattice on
+// the private stream (nothing runs) and instantiates them as graph[key].
+int capture_graph(lbm_ctx *c, int key, int G)
+{
+    if (c->graph[key]) {
+        cudaGraphExecDestroy(c->graph[key]);
+        c->graph[key] = nullptr;
+    }
+    if (!c->cap_stream &&
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    cudaStream_t user = c->stream;
+    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    c->stream = c->cap_stream;
+    int rc = LBM_OK, cur = c->cur;
+    for (int i = 0; i < G && rc == LBM_OK; ++i) {
+        rc = launch_one_step(c, c->step + i, cur);
+        cur = 1 - cur;
+    }
+    c->stream = user;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (rc != LBM_OK || e != cudaSuccess || !g) {
+        if (g)
+            cudaGraphDestroy(g);
+        (void)cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&c->graph[key], g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        c->graph[key] = nullptr;
+        (void)cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    c->graph_version[key] = c->param_version;
+    c->graph_len[key] = G;
+    return LBM_OK;
+}
+
+}  // namespace
+
+int lbm_set_graph_steps(lbm_ctx *c, int steps)
+{
+    if (!c || steps < -1 || (steps > 0 && steps % 2 != 0))
+        return LBM_ERR_ARG;
+    c->graph_mode = steps;
     return LBM_OK;
 }
 
@@ -655,21 +756,36 @@ int lbm_step(lbm_ctx *c, int64_t n)
         return LBM_ERR_ARG;
     if (!c->initialized)
         return LBM_ERR_STATE;
-    for (int64_t i = 0; i < n; ++i) {
-        int rc;
-        if (c->opts.aa) {
-            const int pat = (c->step % 2 == 0) ? PAT_GATHER : PAT_LOCAL;
-            rc = ctx_launch_step(c, c->f[0], c->f[0], pat, nullptr);
-        } else {
-            rc = ctx_launch_step(c, c->f[c->cur], c->f[1 - c->cur], PAT_PULL, nullptr);
-            if (rc == LBM_OK)
-                c->cur = 1 - c->cur;
-        }
+    const int G = graph_steps(c);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool capturing = cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess ||
+                           cs != cudaStreamCaptureStatusNone;
+    if (capturing)
+        (void)cudaGetLastError();
+    if (G >= 2 && n >= 2 * (int64_t)G && !capturing) {
+        // a first direct step does the lazy set-up (node lists, occupancy
+        // queries), which cannot run under capture
+        int rc = step_direct(c, 1);
         if (rc != LBM_OK)
             return rc;
-        ++c->step;
+        n -= 1;
+        // the G-step sequence (G even) repeats from the same AA parity or
+        // pull lattice: one cached graph per starting parity / lattice
+        const int key = c->opts.aa ? (int)(c->step % 2) : c->cur;
+        bool ok = c->graph[key] && c->graph_version[key] == c->param_version &&
+                  c->graph_len[key] == G;
+        if (!ok)
+            ok = capture_graph(c, key, G) == LBM_OK;
+        if (ok) {
+            while (n >= G) {
+                if (cudaGraphLaunch(c->graph[key], c->stream) != cudaSuccess)
+                    return LBM_ERR_CUDA;
+                c->step += G;
+                n -= G;
+            }
+        }
     }
-    return LBM_OK;
+    return step_direct(c, n);
 }
 
 int64_t lbm_step_count(const lbm_ctx *c) { return c ? c->step : -1; }
@@ -685,6 +801,7 @@ int lbm_set_kernel_variant(lbm_ctx *c, int variant)
     if (c->geo && variant == LBM_KERNEL_STAGED)
         return LBM_ERR_ARG;
     c->kernel_variant = variant;
+    ++c->param_version;
     return LBM_OK;
 }
 
@@ -870,7 +987,15 @@ const char *lbm_error_string(int status)
     return "unknown status";
 }
 
-void lbm_destroy(lbm_ctx *c) { delete c; }
+void lbm_destroy(lbm_ctx *c)
+{
+    if (!c)
+        return;
+    drop_graphs(c);
+    if (c->cap_stream)
+        cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
 
 }  // extern "C"
 

@@ -46,6 +46,13 @@ struct lbm_ctx {
     bool list_ready;
     bool list_pairs;            // the list was built for the paired kernel
     long long n_general;        // entries of nlist
+    // CUDA graphs of lbm_step's launches (launch-bound small problems)
+    int graph_mode;            // -1 automatic, 0 off, else steps per graph (even)
+    long long param_version;   // bumped by every change of the launch parameters
+    cudaStream_t cap_stream;   // private stream the graphs are captured on
+    cudaGraphExec_t graph[2];  // by the starting AA parity / pull lattice
+    long long graph_version[2];
+    int graph_len[2];
     lbm::StepParams sp;
     // adjoint run recorded by lbm_adjoint_forward for lbm_adjoint_backward
     int64_t adj_T, adj_K;

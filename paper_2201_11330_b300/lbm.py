@@ -41,7 +41,7 @@ QD = {LBM_D2Q9: (9, 2), LBM_D3Q19: (19, 3), LBM_D3Q27: (27, 3)}
 EXPORTS = [
     "lbm_default_opts", "lbm_tau_from_paper", "lbm_workspace_bytes", "lbm_create",
     "lbm_set_stream", "lbm_init", "lbm_set_force", "lbm_set_lid", "lbm_set_geometry",
-    "lbm_set_inlet", "lbm_step_force", "lbm_step",
+    "lbm_set_inlet", "lbm_step_force", "lbm_set_graph_steps", "lbm_step",
     "lbm_step_count", "lbm_set_kernel_variant", "lbm_kernel_variant_in_use",
     "lbm_step_reduce", "lbm_macroscopic", "lbm_reduce", "lbm_state_bytes", "lbm_get_state",
     "lbm_set_state", "lbm_adjoint_workspace_bytes", "lbm_adjoint_forward",
@@ -96,6 +96,7 @@ def load():
         "lbm_set_geometry": (ip, [_vp, _vp]),
         "lbm_set_inlet": (ip, [_vp, _vp]),
         "lbm_step_force": (ip, [_vp, _i64, _dp]),
+        "lbm_set_graph_steps": (ip, [_vp, ip]),
         "lbm_step": (ip, [_vp, _i64]),
         "lbm_step_count": (_i64, [_vp]),
         "lbm_set_kernel_variant": (ip, [_vp, ip]),
@@ -175,6 +176,10 @@ def lbm_step_force(ctx, n: int):
     out = (ctypes.c_double * 3)()
     _check(load().lbm_step_force(ctx, int(n), out), "lbm_step_force")
     return list(out)
+
+
+def lbm_set_graph_steps(ctx, steps: int):
+    _check(load().lbm_set_graph_steps(ctx, int(steps)), "lbm_set_graph_steps")
 
 
 def lbm_step(ctx, n: int):
@@ -419,6 +424,11 @@ class Lattice:
     def step(self, n=1):
         self._sync_stream()
         lbm_step(self.ctx, n)
+        return self
+
+    def set_graph_steps(self, steps):
+        """CUDA-graph replays of `steps` steps in step() (0 off, -1 automatic)."""
+        lbm_set_graph_steps(self.ctx, steps)
         return self
 
     @property

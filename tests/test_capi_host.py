@@ -116,6 +116,11 @@ def test_state_machine_errors_without_launch(lib):
         assert lib.lbm_set_lid(ctx, bad) == lbm.LBM_ERR_ARG
         assert lib.lbm_state_bytes(ctx) == 19 * 512 * 4
         assert lib.lbm_adjoint_workspace_bytes(ctx, 0, 1) == 0
+        # graph replays: even step counts, 0 (off) or -1 (automatic)
+        for bad in (3, -2, 1):
+            assert lib.lbm_set_graph_steps(ctx, bad) == lbm.LBM_ERR_ARG
+        for good in (0, 2, 32, -1):
+            assert lib.lbm_set_graph_steps(ctx, good) == lbm.LBM_OK
     finally:
         lib.lbm_destroy(ctx)
     o = lbm.lbm_default_opts()

@@ -500,3 +500,60 @@ def test_step_reduce_matches_reduce(lattice, shape, bc, storage, aa):
         assert np.allclose(a["momentum"], b["momentum"], rtol=0, atol=tol * N * 0.05)
         assert abs(a["kinetic_energy"] - b["kinetic_energy"]) <= rel * a["kinetic_energy"]
         assert abs(a["max_speed"] - b["max_speed"]) <= rel * a["max_speed"]
+
+
+# ---------------------------------------------------------------------------
+# CUDA-graph replays of lbm_step: bit for bit the direct launches, also
+# across parameter changes between calls
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s", "f64"])
+@pytest.mark.parametrize("aa", [False, True])
+def test_graph_replays_equal_direct_launches(storage, aa):
+    from paper_2201_11330_b300.lbm import Lattice
+    shape = (37, 22, 19)
+    p0, u0 = W.random_smooth_state(*shape, 3, amp_u=0.04, seed=51)
+    F1 = torch.from_numpy(W.fourier_force(*shape, amplitude=2e-5, seed=1, dims=3)).cuda()
+    F2 = torch.from_numpy(W.fourier_force(*shape, amplitude=2e-5, seed=2, dims=3)).cuda()
+    outs = []
+    for graph in (0, 4):
+        lat = Lattice("d3q19", *shape, 0.6, "cavity", storage=storage, aa=aa, lid=(0.05, 0, 0),
+                      has_force=True)
+        lat.set_graph_steps(graph)
+        lat.set_force(F1)
+        lat.init(torch.from_numpy(p0).cuda(), torch.from_numpy(u0).cuda())
+        lat.step(17)              # odd: the next call starts on an odd step
+        lat.set_lid((0.07, 0, 0.01))
+        lat.step(13)
+        lat.set_force(F2)         # a new force pointer must reach the replays
+        lat.step(21)
+        r = lat.step_reduce(1)
+        p, u = lat.macroscopic()
+        outs.append((p.cpu().numpy(), u.cpu().numpy(), r["kinetic_energy"], lat.step_count))
+    assert outs[0][3] == outs[1][3] == 52
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]
+
+
+def test_graph_replays_with_faces_and_obstacles():
+    from paper_2201_11330_b300.lbm import Lattice
+    nx, ny, nz = 40, 18, 12
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    sol = ((x - 12) ** 2 + (y - 9) ** 2 + (z - 6) ** 2 <= 9).astype(np.uint8)
+    inl = torch.zeros((3, ny * nz), device="cuda")
+    inl[0] = 0.04
+    outs = []
+    for graph in (0, 6):
+        lat = Lattice("d3q27", nx, ny, nz, 0.6, ["inlet", "outflow", "symmetry", "symmetry",
+                                                 "periodic", "periodic"],
+                      storage="f32", obstacles=True)
+        lat.set_graph_steps(graph)
+        lat.set_geometry(torch.from_numpy(sol.ravel()).cuda())
+        lat.set_inlet(inl)
+        lat.init()
+        lat.step(40)
+        f = lat.step_force(1)
+        p, u = lat.macroscopic()
+        outs.append((p.cpu().numpy(), u.cpu().numpy(), f))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]
