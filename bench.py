@@ -263,7 +263,8 @@ def run_sphere(storage, steps, warmup, world, device):
     f = lat.step_force(1)
     bpn = 2 * 27 * BYTES_OF[storage] + 4
     out = {"glups": replica_value(N, steps, total, world), "ms_per_step": total / steps,
-           "bytes_per_node": bpn, "nodes": N, "drag_force_x": f[0]}
+           "bytes_per_node": bpn, "nodes": N, "drag_force_x": f[0],
+           "traffic_per_step": load_traffic(f"sphere_{storage}")}
     del lat
     torch.cuda.empty_cache()
     return out
