@@ -270,6 +270,49 @@ def run_sphere(storage, steps, warmup, world, device):
     return out
 
 
+def run_config_lines(world, device):
+    """Device throughput on the other configurations' workloads: the 64^2
+    D2Q9 cavity (FP64, Re 100, 1000 steps), the 512^2 Taylor-Green vortex
+    (FP64 and FP32, tau 0.8, 5000 steps) and the 256^3 D3Q19 cavity (Re 1000,
+    AA, FP32 and FP16S).  Event-timed lbm_step(n) calls (CUDA-graph replays
+    where the library takes them)."""
+    import torch
+    from paper_2201_11330_b300 import workloads as W
+    from paper_2201_11330_b300.lbm import Lattice
+    out = {}
+
+    def timed(name, lat, steps, N):
+        lat.step(8)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lat.step(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"glups": N * steps / (ms * 1e-3) / 1e9 * world, "ms": ms, "steps": steps,
+                     "us_per_step": ms * 1e3 / steps}
+
+    c = W.cavity_params(64, 100.0, 0.1)
+    lat = Lattice("d2q9", 64, 64, 1, c["tau"], "cavity", storage="f64", lid=c["lid"])
+    lat.init()
+    timed("d2q9_cavity64_re100_f64", lat, 1000, 64 * 64)
+    p0, u0 = W.taylor_green_2d(512, 512, 0.05)
+    for st in ("f64", "f32"):
+        lat = Lattice("d2q9", 512, 512, 1, 0.8, "periodic", storage=st)
+        lat.init(torch.from_numpy(p0).to(device), torch.from_numpy(u0).to(device))
+        timed(f"d2q9_tgv512_{st}", lat, 5000, 512 * 512)
+    c = W.cavity_params(256, 1000.0, 0.1)
+    for st in ("f32", "f16s"):
+        lat = Lattice("d3q19", 256, 256, 256, c["tau"], "cavity", storage=st, aa=True,
+                      lid=c["lid"])
+        lat.init()
+        timed(f"d3q19_cavity256_re1000_{st}_aa", lat, 200, 256 ** 3)
+    del lat
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_e2e(n, re, storage, steps, warmup, world, device):
     """Public API with host buffers: pinned-host initial fields -> device,
     lbm_init, then per step lbm_step_reduce (the step with the Monitor fused
@@ -371,10 +414,32 @@ def cpu_baseline_sample(target_s=12.0):
     t0 = time.perf_counter()
     oracle.run("d3q19", n, n, n, c["tau"], "cavity", steps, lid=c["lid"], threads=cores)
     dt = time.perf_counter() - t0
-    return {"value": n ** 3 * steps / dt / 1e9, "unit": "GLUPS", "cores": cores,
-            "kind": "oracle",
-            "sample": f"D3Q19 cavity {n}^3 at the 512^3 workload's tau={c['tau']}, {steps} steps "
-                      f"(init + steps + moments timed), {dt:.1f} s, OpenMP threads={cores}"}
+    out = {"value": n ** 3 * steps / dt / 1e9, "unit": "GLUPS", "cores": cores,
+           "kind": "oracle",
+           "sample": f"D3Q19 cavity {n}^3 at the 512^3 workload's tau={c['tau']}, {steps} steps "
+                     f"(init + steps + moments timed), {dt:.1f} s, OpenMP threads={cores}"}
+    # the oracle on the other configurations' shapes (a few seconds in all)
+    cfg = {}
+
+    def timed(name, threads, *a, **kw):
+        t0 = time.perf_counter()
+        oracle.run(*a, threads=threads, **kw)
+        dt = time.perf_counter() - t0
+        nx, ny, nz, steps = a[1], a[2], a[3], a[6]
+        cfg[name] = {"mlups": nx * ny * nz * steps / dt / 1e6, "threads": threads,
+                     "steps": steps, "s": round(dt, 3)}
+
+    c64 = W.cavity_params(64, 100.0, 0.1)
+    timed("d2q9_cavity64_re100", cores, "d2q9", 64, 64, 1, c64["tau"], "cavity", 1000,
+          lid=c64["lid"])
+    p0, u0 = W.taylor_green_2d(512, 512, 0.05)
+    timed("d2q9_tgv512", cores, "d2q9", 512, 512, 1, 0.8, "periodic", 20, p0=p0, u0=u0)
+    c3 = W.cavity_params(64, 1000.0, 0.1)
+    for threads in (1, cores):
+        timed(f"d3q19_cavity64_re1000_threads{threads}", threads, "d3q19", 64, 64, 64, c3["tau"],
+              "cavity", 10, lid=c3["lid"])
+    out["configs"] = cfg
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -506,6 +571,7 @@ def main():
             r = run_sphere(st, max(10, args.steps // 2), args.warmup, world, device)
             r["hbm_frac"] = r["glups"] / world * r["bytes_per_node"] / peak
             extras[f"sphere_d3q27_512x128x128_{st}"] = r
+        extras["configs"] = run_config_lines(world, device)
         try:
             extras["adjoint"] = run_adjoint(128, 2000, 100, world, device)
         except Exception as exc:  # reported, not hidden
