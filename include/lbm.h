@@ -348,7 +348,8 @@ int lbm_reduce_state_noalloc(int lattice, int nx, int ny, int nz, int bc, const 
 /* Static description of a status code. */
 const char *lbm_error_string(int status);
 
-/* Free the host-side context (the workspace stays the caller's). */
+/* Free the host-side context and its graphs, if any (after the context's
+ * stream has finished their replays; the workspace stays the caller's). */
 void lbm_destroy(lbm_ctx *ctx);
 
 #ifdef __cplusplus

@@ -991,6 +991,8 @@ void lbm_destroy(lbm_ctx *c)
 {
     if (!c)
         return;
+    if (c->graph[0] || c->graph[1])  // no replay may still be running
+        cudaStreamSynchronize(c->stream);
     drop_graphs(c);
     if (c->cap_stream)
         cudaStreamDestroy(c->cap_stream);

@@ -633,11 +633,7 @@ __global__ void __launch_bounds__(256) k_step_skip(const typename Sto<S>::T *src
 }
 
 // ---- initialisation (Sec. 2.2: f = feq(p, u), then the first collision) -----
-struct InitParams {
-    const double *p0;  // N or NULL (p = 1/3)
-    const double *u0;  // d*N or NULL (u = 0)
-    int compressible_unused;
-};
+// p0: N values or NULL (p = 1/3); u0: d*N values or NULL (u = 0).
 
 template <class L, int S, bool AA, int MODEL, bool FORCE>
 __global__ void __launch_bounds__(256) k_init(typename Sto<S>::T *dst, const StepParams p,
