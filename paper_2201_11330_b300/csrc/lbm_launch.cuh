@@ -89,7 +89,12 @@ cudaError_t launch_storage(const Launch &l)
                     auto *d16 = (unsigned short *)l.dst;
                     return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
                         constexpr bool rd = decltype(Rd)::value;
-                        if (l.pattern == PAT_PULL)
+                        constexpr bool occ6 = L::Q == 27 && !rd;
+                        if (l.pattern == PAT_PULL && occ6)
+                            k_step_pair_occ6<L, S, PAT_PULL, c, fo><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                        else if (l.pattern == PAT_GATHER && occ6)
+                            k_step_pair_occ6<L, S, PAT_GATHER, c, fo><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                        else if (l.pattern == PAT_PULL)
                             k_step_pair<L, S, PAT_PULL, c, fo, rd><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
                         else if (l.pattern == PAT_GATHER)
                             k_step_pair<L, S, PAT_GATHER, c, fo, rd><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
