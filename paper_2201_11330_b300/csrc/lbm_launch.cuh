@@ -89,17 +89,34 @@ cudaError_t launch_storage(const Launch &l)
                     auto *d16 = (unsigned short *)l.dst;
                     return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
                         constexpr bool rd = decltype(Rd)::value;
-                        constexpr bool occ6 = L::Q == 27 && !rd;
-                        if (l.pattern == PAT_PULL && occ6)
-                            k_step_pair_occ6<L, S, PAT_PULL, c, fo><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
-                        else if (l.pattern == PAT_GATHER && occ6)
-                            k_step_pair_occ6<L, S, PAT_GATHER, c, fo><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
-                        else if (l.pattern == PAT_PULL)
-                            k_step_pair<L, S, PAT_PULL, c, fo, rd><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
-                        else if (l.pattern == PAT_GATHER)
-                            k_step_pair<L, S, PAT_GATHER, c, fo, rd><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
-                        else
-                            k_step_pair<L, S, PAT_LOCAL, c, fo, rd><<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                        // measured: D3Q27 pull and gather at six blocks per SM,
+                        // D3Q19 pull at eight (its gather is issue-bound and
+                        // spills when bounded)
+                        constexpr int minb = L::Q == 27 ? 6 : L::Q == 19 ? 8 : 0;
+                        if constexpr (minb > 0 && !rd) {
+                            if (l.pattern == PAT_PULL)
+                                k_step_pair_bounded<L, S, PAT_PULL, c, fo, minb>
+                                    <<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                            else if (l.pattern == PAT_GATHER && L::Q == 27)
+                                k_step_pair_bounded<L, S, PAT_GATHER, c, fo, minb>
+                                    <<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                            else if (l.pattern == PAT_GATHER)
+                                k_step_pair<L, S, PAT_GATHER, c, fo, rd>
+                                    <<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                            else
+                                k_step_pair<L, S, PAT_LOCAL, c, fo, rd>
+                                    <<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                        } else {
+                            if (l.pattern == PAT_PULL)
+                                k_step_pair<L, S, PAT_PULL, c, fo, rd>
+                                    <<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                            else if (l.pattern == PAT_GATHER)
+                                k_step_pair<L, S, PAT_GATHER, c, fo, rd>
+                                    <<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                            else
+                                k_step_pair<L, S, PAT_LOCAL, c, fo, rd>
+                                    <<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
+                        }
                         return cudaGetLastError();
                     });
                 });

@@ -468,7 +468,8 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
 
 // The pull step of a box with per-face boundaries or obstacles on the pairs
 // the paired kernel can update (see k_step_skip).  MON: 0, 1 = monitor sums,
-// 2 = obstacle force (zero here).  Six blocks per SM, as k_step_pair_occ6.
+// 2 = obstacle force (zero here).  Six blocks per SM, as the bounded D3Q27
+// kernels.
 template <class L, int S, int MODEL, bool FORCE, int MON>
 __global__ void __launch_bounds__(kPairThreads, 6) k_step_pair_skip(const unsigned short *src,
                                                                  unsigned short *dst,
@@ -486,12 +487,14 @@ __global__ void __launch_bounds__(kPairThreads, 6) k_step_pair_skip(const unsign
         pair_body<L, S, PAT_PULL, MODEL, FORCE, false, MON == 1, true>(src, dst, p);
 }
 
-// D3Q27 pull and AA gather: held to six blocks per SM (80 registers, a few
-// bytes spilled in the gather) instead of the 90-94 they take unbounded.
-template <class L, int S, int PAT, int MODEL, bool FORCE>
-__global__ void __launch_bounds__(kPairThreads, 6) k_step_pair_occ6(const unsigned short *src,
-                                                                    unsigned short *dst,
-                                                                    const StepParams p)
+// Pull (and for D3Q27 the AA gather) held to MINB blocks per SM: D3Q27 six
+// (90-94 -> 80 registers), D3Q19 eight (82 -> 64); without the bound the
+// compiler takes more registers than these memory-latency-bound kernels can
+// afford.
+template <class L, int S, int PAT, int MODEL, bool FORCE, int MINB>
+__global__ void __launch_bounds__(kPairThreads, MINB) k_step_pair_bounded(const unsigned short *src,
+                                                                          unsigned short *dst,
+                                                                          const StepParams p)
 {
     const int y = blockIdx.y, z = blockIdx.z;
     const bool irow = y > 0 && y < p.ny - 1 && (L::D == 2 || (z > 0 && z < p.nz - 1));
