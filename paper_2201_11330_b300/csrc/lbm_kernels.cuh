@@ -564,12 +564,13 @@ __global__ void __launch_bounds__(256) k_step(const typename Sto<S>::T *src,
                                                          blockIdx.z, grid_block_index());
 }
 
-// D3Q27 with 16-bit storage: held to four blocks per SM (64 registers, no
-// spills) instead of the three its 70-72 registers allow unbounded; the loads
-// of these kernels are latency-bound.
-template <class L, int S, int PAT, int MODEL, bool FORCE>
-__global__ void __launch_bounds__(256, 4) k_step_occ4(const typename Sto<S>::T *src,
-                                                      typename Sto<S>::T *dst, const StepParams p)
+// The step held to MINB blocks per SM (D3Q27 with 16-bit storage: the
+// compiler's 70-72 registers leave three blocks per SM to these
+// latency-bound kernels).
+template <class L, int S, int PAT, int MODEL, bool FORCE, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_step_bounded(const typename Sto<S>::T *src,
+                                                            typename Sto<S>::T *dst,
+                                                            const StepParams p)
 {
     step_kernel_body<L, S, PAT, MODEL, FORCE, false, false>(src, dst, p, blockIdx.x, blockIdx.y,
                                                             blockIdx.z, grid_block_index());

@@ -68,9 +68,9 @@ inline cudaError_t with_model(int m, F &&f)
     }
 }
 
-// plain D3Q27 pull / gather kernels with 16-bit storage: the four-block bound
+// plain D3Q27 pull / gather kernels with 16-bit storage: blocks per SM bound
 template <class L, int S>
-constexpr bool kOcc4 = L::Q == 27 && (S == ST_F16S || S == ST_BF16S);
+constexpr int kPlainMinBlocks = (L::Q == 27 && (S == ST_F16S || S == ST_BF16S)) ? 5 : 0;
 
 template <class L, int S>
 cudaError_t launch_storage(const Launch &l)
@@ -215,8 +215,8 @@ cudaError_t launch_storage(const Launch &l)
                     return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
                         constexpr int c = decltype(C)::value;
                         constexpr bool fo = decltype(Fo)::value, rd = decltype(Rd)::value;
-                        if constexpr (kOcc4<L, S> && !rd)
-                            k_step_occ4<L, S, PAT_PULL, c, fo>
+                        if constexpr (kPlainMinBlocks<L, S> > 0 && !rd)
+                            k_step_bounded<L, S, PAT_PULL, c, fo, kPlainMinBlocks<L, S>>
                                 <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
                         else
                             k_step<L, S, PAT_PULL, c, fo, false, rd>
@@ -234,9 +234,9 @@ cudaError_t launch_storage(const Launch &l)
                     if (l.sp.partials != nullptr)
                         k_step_gather_red<L, S, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, dst,
                                                                                          l.sp);
-                    else if constexpr (kOcc4<L, S>)
-                        k_step_occ4<L, S, PAT_GATHER, c, fo><<<l.grid, l.block, 0, l.stream>>>(
-                            src, dst, l.sp);
+                    else if constexpr (kPlainMinBlocks<L, S> > 0)
+                        k_step_bounded<L, S, PAT_GATHER, c, fo, kPlainMinBlocks<L, S>>
+                            <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
                     else
                         k_step<L, S, PAT_GATHER, c, fo, false, false>
                             <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
