@@ -314,8 +314,8 @@ def run_config_lines(world, device):
 
 
 def run_e2e(n, re, storage, steps, warmup, world, device):
-    """Public API with host buffers: pinned-host initial fields -> device,
-    lbm_init, then per step lbm_step_reduce (the step with the Monitor fused
+    """Public API with host buffers: pinned-host FP32 initial fields ->
+    device, lbm_init_f32, then per step lbm_step_reduce (the step with the Monitor fused
     in; 48 B to host), final macroscopic fields -> pinned host.  All inside
     the timed region."""
     import torch
@@ -324,12 +324,12 @@ def run_e2e(n, re, storage, steps, warmup, world, device):
     c = W.cavity_params(n, re, 0.1)
     N = n ** 3
     lat = Lattice("d3q19", n, n, n, c["tau"], "cavity", storage=storage, aa=True, lid=c["lid"])
-    p_host = torch.full((N,), 1.0 / 3.0, dtype=torch.float64).pin_memory()
-    u_host = torch.zeros((3, N), dtype=torch.float64).pin_memory()
+    p_host = torch.full((N,), 1.0 / 3.0, dtype=torch.float32).pin_memory()
+    u_host = torch.zeros((3, N), dtype=torch.float32).pin_memory()
     p_out = torch.empty((N,), dtype=torch.float32).pin_memory()
     u_out = torch.empty((3, N), dtype=torch.float32).pin_memory()
-    p_dev = torch.empty((N,), dtype=torch.float64, device=device)
-    u_dev = torch.empty((3, N), dtype=torch.float64, device=device)
+    p_dev = torch.empty((N,), dtype=torch.float32, device=device)
+    u_dev = torch.empty((3, N), dtype=torch.float32, device=device)
     p_o = torch.empty((N,), dtype=torch.float32, device=device)
     u_o = torch.empty((3, N), dtype=torch.float32, device=device)
 
@@ -351,13 +351,13 @@ def run_e2e(n, re, storage, steps, warmup, world, device):
     job(steps)
     barrier(world)
     dt = max_over_ranks(time.perf_counter() - t0, world, device)
-    h2d = (p_host.numel() + u_host.numel()) * 8
+    h2d = (p_host.numel() + u_host.numel()) * 4
     d2h = (p_out.numel() + u_out.numel()) * 4
     res = {"value": world * N * steps / dt / 1e9, "unit": "GLUPS",
            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": 48 + d2h / steps,
            "steps": steps,
            "what": f"D3Q19 cavity {n}^3 {storage} AA via paper_2201_11330_b300.lbm.Lattice: "
-                   "pinned-host FP64 initial (p, u) -> device, lbm_init, per step "
+                   "pinned-host FP32 initial (p, u) -> device, lbm_init_f32, per step "
                    "lbm_step_reduce(1) (step with the FP64 monitor fused in, 48 B to host), "
                    "final FP32 (p, u) -> pinned host"}
     del lat

@@ -182,6 +182,8 @@ int lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
  * Resets the step counter to 0.  When a force is set, the stored state also
  * holds the first collision (the state is always post-collision). */
 int lbm_init(lbm_ctx *ctx, const double *p, const double *u);
+/* lbm_init with FP32 fields (half the bytes to bring to the device). */
+int lbm_init_f32(lbm_ctx *ctx, const float *p, const float *u);
 
 /* Body force (Guo form, trapezoidal): device FP32 field of d*N values,
  * component-major, borrowed until replaced; NULL removes the force.

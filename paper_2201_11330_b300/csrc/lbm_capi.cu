@@ -566,7 +566,8 @@ int lbm_set_stream(lbm_ctx *c, void *cuda_stream)
     return LBM_OK;
 }
 
-int lbm_init(lbm_ctx *c, const double *p, const double *u)
+namespace {
+int init_from(lbm_ctx *c, const void *p, const void *u, bool in_f32)
 {
     if (!c)
         return LBM_ERR_ARG;
@@ -574,6 +575,7 @@ int lbm_init(lbm_ctx *c, const double *p, const double *u)
     l.pattern = c->opts.aa ? 1 : 0;
     l.p0 = p;
     l.u0 = u;
+    l.in_f32 = in_f32;
     c->cur = 0;
     l.dst = c->f[0];
     c->step = 0;
@@ -584,6 +586,11 @@ int lbm_init(lbm_ctx *c, const double *p, const double *u)
     c->initialized = true;
     return LBM_OK;
 }
+}  // namespace
+
+int lbm_init(lbm_ctx *c, const double *p, const double *u) { return init_from(c, p, u, false); }
+
+int lbm_init_f32(lbm_ctx *c, const float *p, const float *u) { return init_from(c, p, u, true); }
 
 int lbm_set_force(lbm_ctx *c, const float *force)
 {

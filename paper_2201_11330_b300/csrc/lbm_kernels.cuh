@@ -634,11 +634,12 @@ __global__ void __launch_bounds__(256) k_step_skip(const typename Sto<S>::T *src
 }
 
 // ---- initialisation (Sec. 2.2: f = feq(p, u), then the first collision) -----
-// p0: N values or NULL (p = 1/3); u0: d*N values or NULL (u = 0).
+// p0: N values or NULL (p = 1/3); u0: d*N values or NULL (u = 0); IN is
+// their type (FP64, or FP32 for lbm_init_f32).
 
-template <class L, int S, bool AA, int MODEL, bool FORCE>
+template <class L, int S, bool AA, int MODEL, bool FORCE, class IN>
 __global__ void __launch_bounds__(256) k_init(typename Sto<S>::T *dst, const StepParams p,
-                                              const double *p0, const double *u0)
+                                              const IN *p0, const IN *u0)
 {
     constexpr int Q = L::Q;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -650,7 +651,7 @@ __global__ void __launch_bounds__(256) k_init(typename Sto<S>::T *dst, const Ste
     const int n = x + p.nx * (y + p.ny * z);
     const Coef<R> &c = coef<R>(p);
     // shifted pressure P - sigma taken in FP64 before rounding to R
-    const double P = p0 ? 3.0 * p0[n] : 1.0;
+    const double P = p0 ? 3.0 * double(p0[n]) : 1.0;
     const R dP = R(P - double(c.sigma));
     R u[3] = {R(0), R(0), R(0)};
     if (u0)
@@ -936,7 +937,8 @@ struct Launch {
     const void *src;
     void *dst;
     StepParams sp;
-    const double *p0, *u0;
+    const void *p0, *u0;
+    bool in_f32;  // K_INIT: p0 / u0 are FP32 (else FP64)
     MomParams mp;
     AdjParams ap;
     size_t count;  // K_FLUSH

@@ -258,8 +258,14 @@ cudaError_t launch_storage(const Launch &l)
         return with_bool(l.pattern == 1, [&](auto AA) {
             return with_model(l.model, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
-                    k_init<L, S, decltype(AA)::value, decltype(C)::value, decltype(Fo)::value>
-                        <<<l.grid, l.block, 0, l.stream>>>(dst, l.sp, l.p0, l.u0);
+                    constexpr bool aa = decltype(AA)::value, fo = decltype(Fo)::value;
+                    constexpr int c = decltype(C)::value;
+                    if (l.in_f32)
+                        k_init<L, S, aa, c, fo, float><<<l.grid, l.block, 0, l.stream>>>(
+                            dst, l.sp, (const float *)l.p0, (const float *)l.u0);
+                    else
+                        k_init<L, S, aa, c, fo, double><<<l.grid, l.block, 0, l.stream>>>(
+                            dst, l.sp, (const double *)l.p0, (const double *)l.u0);
                     return cudaGetLastError();
                 });
             });

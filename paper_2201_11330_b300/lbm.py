@@ -40,7 +40,7 @@ QD = {LBM_D2Q9: (9, 2), LBM_D3Q19: (19, 3), LBM_D3Q27: (27, 3)}
 # Every extern "C" symbol include/lbm.h declares.
 EXPORTS = [
     "lbm_default_opts", "lbm_tau_from_paper", "lbm_workspace_bytes", "lbm_create",
-    "lbm_set_stream", "lbm_init", "lbm_set_force", "lbm_set_lid", "lbm_set_geometry",
+    "lbm_set_stream", "lbm_init", "lbm_init_f32", "lbm_set_force", "lbm_set_lid", "lbm_set_geometry",
     "lbm_set_inlet", "lbm_step_force", "lbm_set_graph_steps", "lbm_step",
     "lbm_step_count", "lbm_set_kernel_variant", "lbm_kernel_variant_in_use",
     "lbm_step_reduce", "lbm_macroscopic", "lbm_reduce", "lbm_state_bytes", "lbm_get_state",
@@ -91,6 +91,7 @@ def load():
                             ctypes.POINTER(_vp)]),
         "lbm_set_stream": (ip, [_vp, _vp]),
         "lbm_init": (ip, [_vp, _vp, _vp]),
+        "lbm_init_f32": (ip, [_vp, _vp, _vp]),
         "lbm_set_force": (ip, [_vp, _vp]),
         "lbm_set_lid": (ip, [_vp, _dp]),
         "lbm_set_geometry": (ip, [_vp, _vp]),
@@ -153,6 +154,10 @@ def lbm_set_stream(ctx, stream_ptr):
 
 def lbm_init(ctx, p_ptr, u_ptr):
     _check(load().lbm_init(ctx, p_ptr, u_ptr), "lbm_init")
+
+
+def lbm_init_f32(ctx, p_ptr, u_ptr):
+    _check(load().lbm_init_f32(ctx, p_ptr, u_ptr), "lbm_init_f32")
 
 
 def lbm_set_force(ctx, force_ptr):
@@ -362,13 +367,19 @@ class Lattice:
         return t
 
     def init(self, p=None, u=None):
-        """f = feq(p, u) (Sec. 2.2); p (N,) and u (d, N) FP64, None = 1/3 and 0."""
+        """f = feq(p, u) (Sec. 2.2); p (N,) and u (d, N), None = 1/3 and 0.
+        FP32 tensors (both, or the one given) go through lbm_init_f32, anything
+        else is taken as FP64."""
         torch = self.torch
         self._sync_stream()
-        pt = None if p is None else self._dev(p, torch.float64, self.N)
-        ut = None if u is None else self._dev(u, torch.float64, self.d * self.N)
-        lbm_init(self.ctx, None if pt is None else pt.data_ptr(),
-                 None if ut is None else ut.data_ptr())
+        given = [t for t in (p, u) if t is not None]
+        f32 = bool(given) and all(isinstance(t, torch.Tensor) and t.dtype == torch.float32
+                                  for t in given)
+        dt = torch.float32 if f32 else torch.float64
+        pt = None if p is None else self._dev(p, dt, self.N)
+        ut = None if u is None else self._dev(u, dt, self.d * self.N)
+        (lbm_init_f32 if f32 else lbm_init)(self.ctx, None if pt is None else pt.data_ptr(),
+                                            None if ut is None else ut.data_ptr())
         # keep the inputs alive until the init kernel has consumed them
         self._init_inputs = (pt, ut)
         return self

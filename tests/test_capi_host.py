@@ -22,7 +22,7 @@ def lib():
 def _header_functions():
     text = open(os.path.join(ROOT, "include", "lbm.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_matches_binding():

@@ -557,3 +557,21 @@ def test_graph_replays_with_faces_and_obstacles():
         outs.append((p.cpu().numpy(), u.cpu().numpy(), f))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
     assert outs[0][2] == outs[1][2]
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_init_from_fp32_fields(storage):
+    """lbm_init_f32 equals lbm_init on the same (FP32-representable) fields."""
+    from paper_2201_11330_b300.lbm import Lattice
+    shape = (33, 20, 17)
+    p0, u0 = W.random_smooth_state(*shape, 3, amp_u=0.04, seed=52)
+    p0 = p0.astype(np.float32).astype(np.float64)
+    u0 = u0.astype(np.float32).astype(np.float64)
+    outs = []
+    for dt in (torch.float64, torch.float32):
+        lat = Lattice("d3q19", *shape, 0.6, "cavity", storage=storage, aa=True, lid=(0.05, 0, 0))
+        lat.init(torch.from_numpy(p0).to("cuda", dt), torch.from_numpy(u0).to("cuda", dt))
+        lat.step(5)
+        p, u = lat.macroscopic()
+        outs.append((p.cpu().numpy(), u.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
