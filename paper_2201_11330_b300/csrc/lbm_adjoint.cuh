@@ -23,7 +23,9 @@
 namespace lbm {
 
 
-template <class L, class R, bool FORCE>
+// INTERIOR: the node's row has neighbours inside the box in y and z (no wall,
+// no wrap), so only the x axis needs per-thread boundary logic.
+template <class L, class R, bool FORCE, bool INTERIOR>
 __device__ __forceinline__ void adjoint_node(const StepParams &p, const AdjParams &ap, int x,
                                              int y, int z, R (&gu)[3])
 {
@@ -33,8 +35,8 @@ __device__ __forceinline__ void adjoint_node(const StepParams &p, const AdjParam
     const int n = x + p.nx * (y + p.ny * z);
     const R *lam = (const R *)ap.lam_in;
     AxisNbr X, Y, Z;
-    make_axes<L, false>(p, x, y, z, X, Y, Z);
-    const bool lid_row = p.lid_on && (y == p.ny - 1);
+    make_axes<L, INTERIOR>(p, x, y, z, X, Y, Z);
+    const bool lid_row = !INTERIOR && p.lid_on && (y == p.ny - 1);
     R mu[Q];
     SFor<0, Q>::run([&](auto B_) {
         constexpr int b = decltype(B_)::value;
@@ -147,8 +149,13 @@ __global__ void __launch_bounds__(256) k_adjoint(const StepParams p, const AdjPa
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     R gu[3] = {R(0), R(0), R(0)};
-    if (x < p.nx)
-        adjoint_node<L, R, FORCE>(p, ap, x, y, z, gu);
+    if (x < p.nx) {
+        const bool interior = y > 0 && y < p.ny - 1 && (L::D == 2 || (z > 0 && z < p.nz - 1));
+        if (interior)
+            adjoint_node<L, R, FORCE, true>(p, ap, x, y, z, gu);
+        else
+            adjoint_node<L, R, FORCE, false>(p, ap, x, y, z, gu);
+    }
     if (!(p.lid_on && y == p.ny - 1))
         return;  // block-uniform
     __shared__ double sh[8][3];
