@@ -132,7 +132,8 @@ typedef enum { LBM_COLL_BGK = 0, LBM_COLL_TRT = 1 } lbm_collision;
 typedef struct {
     int storage;        /* lbm_storage */
     int aa;             /* 0: two-lattice pull scheme; 1: single-lattice AA pattern */
-    int compressible;   /* 0: Eq. (incompressible_feq); 1: Eq. (feq) with rho = sum f */
+    int compressible;   /* 0: Eq. (incompressible_feq); 1: Eq. (feq) with rho = sum f
+                           (FP64 / FP32 storage only) */
     int f32_unshifted;  /* LBM_F32 only: store f itself instead of f - t */
     double rho0;        /* constant density of the incompressible model (> 0) */
     double lid_u[3];    /* moving-wall velocity (ignored for LBM_BC_PERIODIC) */
@@ -245,7 +246,8 @@ int64_t lbm_step_count(const lbm_ctx *ctx);
  *                     direction in shared memory with bulk asynchronous copies
  *                     (cp.async.bulk + mbarrier, several segments in flight);
  *                     needs nx to be a multiple of 16 bytes' worth of values
- *                     (8 for 16-bit storage, 4 for FP32, 2 for FP64);
+ *                     (8 for 16-bit storage, 4 for FP32, 2 for FP64) and the
+ *                     incompressible BGK model;
  *   LBM_KERNEL_PAIRED 16-bit storage only, nx even: two adjacent nodes per
  *                     thread, one 32-bit word per slot, e_x = +-1 directions
  *                     realigned with warp shuffles;

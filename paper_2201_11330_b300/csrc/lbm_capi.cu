@@ -55,6 +55,8 @@ bool valid_opts(const lbm_opts &o)
     if (o.collision == LBM_COLL_TRT &&
         (o.compressible || !(o.trt_lambda > 0.0 && isfinite(o.trt_lambda))))
         return false;
+    if (o.compressible && (o.storage == LBM_F16S || o.storage == LBM_BF16S))
+        return false;  // the compressible model is built for FP64 / FP32 storage
     if (!(o.rho0 > 0.0) || !isfinite(o.rho0))
         return false;
     if (o.geometry != 0 && o.geometry != 1)
@@ -252,7 +254,8 @@ void keep_inlet(lbm_ctx *c, const float *inlet) { c->sp.inlet = inlet; }
 bool bulk_eligible(const lbm_ctx *c)
 {
     const int per16 = 16 / (int)storage_elem(c->opts.storage);
-    return c->nx % per16 == 0;
+    const bool bgk_inc = !c->opts.compressible && c->opts.collision == LBM_COLL_BGK;
+    return bgk_inc && c->nx % per16 == 0;
 }
 
 // The paired kernel moves two 16-bit values per thread and slot.

@@ -52,15 +52,20 @@ inline cudaError_t with_bool(bool b, F &&f)
 template <int M>
 using model_c = std::integral_constant<int, M>;
 
-// one instantiation per collision model (Model)
-template <class F>
+// one instantiation per collision model (Model); the compressible model is
+// built for FP64 and FP32 storage only (lbm_create refuses it with 16-bit
+// storage), which keeps the 16-bit translation units' build time down
+template <int S, class F>
 inline cudaError_t with_model(int m, F &&f)
 {
     switch (m) {
     case M_INC:
         return f(model_c<M_INC>{});
     case M_COMP:
-        return f(model_c<M_COMP>{});
+        if constexpr (S == ST_F64 || S == ST_F32)
+            return f(model_c<M_COMP>{});
+        else
+            return cudaErrorInvalidValue;
     case M_TRT:
         return f(model_c<M_TRT>{});
     default:
@@ -81,7 +86,7 @@ cudaError_t launch_storage(const Launch &l)
     if (l.kind == K_STEP && l.pair && !l.skip) {
         if constexpr (S == ST_F16S || S == ST_BF16S) {
             const dim3 grid((l.sp.nx + 2 * kPairThreads - 1) / (2 * kPairThreads), l.sp.ny, l.sp.nz);
-            return with_model(l.model, [&](auto C) {
+            return with_model<S>(l.model, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
                     constexpr int c = decltype(C)::value;
                     constexpr bool fo = decltype(Fo)::value;
@@ -126,7 +131,7 @@ cudaError_t launch_storage(const Launch &l)
         }
     }
     if (l.kind == K_STEP && l.geo) {
-        return with_model(l.model, [&](auto C) {
+        return with_model<S>(l.model, [&](auto C) {
             return with_bool(l.force, [&](auto Fo) {
                 constexpr int c = decltype(C)::value;
                 constexpr bool fo = decltype(Fo)::value;
@@ -141,7 +146,7 @@ cudaError_t launch_storage(const Launch &l)
         });
     }
     if (l.kind == K_STEP && l.skip) {
-        return with_model(l.model, [&](auto C) {
+        return with_model<S>(l.model, [&](auto C) {
             return with_bool(l.force, [&](auto Fo) {
                 constexpr int c = decltype(C)::value;
                 constexpr bool fo = decltype(Fo)::value;
@@ -187,17 +192,16 @@ cudaError_t launch_storage(const Launch &l)
             return cudaErrorInvalidValue;
         }
     }
-    if (l.kind == K_STEP && l.bulk) {
-        return with_model(l.model, [&](auto C) {
-            return with_bool(l.force, [&](auto Fo) {
-                constexpr int c = decltype(C)::value;
-                constexpr bool fo = decltype(Fo)::value;
-                if (l.pattern == PAT_PULL)
-                    return launch_bulk<L, S, PAT_PULL, c, fo>(l);
-                if (l.pattern == PAT_GATHER)
-                    return launch_bulk<L, S, PAT_GATHER, c, fo>(l);
-                return launch_bulk<L, S, PAT_LOCAL, c, fo>(l);
-            });
+    if (l.kind == K_STEP && l.bulk) {  // the staged variant: incompressible BGK only
+        if (l.model != M_INC)
+            return cudaErrorInvalidValue;
+        return with_bool(l.force, [&](auto Fo) {
+            constexpr bool fo = decltype(Fo)::value;
+            if (l.pattern == PAT_PULL)
+                return launch_bulk<L, S, PAT_PULL, M_INC, fo>(l);
+            if (l.pattern == PAT_GATHER)
+                return launch_bulk<L, S, PAT_GATHER, M_INC, fo>(l);
+            return launch_bulk<L, S, PAT_LOCAL, M_INC, fo>(l);
         });
     }
     if (l.kind == K_STEP) {
@@ -210,7 +214,7 @@ cudaError_t launch_storage(const Launch &l)
                     return cudaGetLastError();
                 });
             }
-            return with_model(l.model, [&](auto C) {
+            return with_model<S>(l.model, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
                     return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
                         constexpr int c = decltype(C)::value;
@@ -227,7 +231,7 @@ cudaError_t launch_storage(const Launch &l)
             });
         }
         if (l.pattern == PAT_GATHER) {
-            return with_model(l.model, [&](auto C) {
+            return with_model<S>(l.model, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
                     constexpr int c = decltype(C)::value;
                     constexpr bool fo = decltype(Fo)::value;
@@ -244,7 +248,7 @@ cudaError_t launch_storage(const Launch &l)
                 });
             });
         }
-        return with_model(l.model, [&](auto C) {
+        return with_model<S>(l.model, [&](auto C) {
             return with_bool(l.force, [&](auto Fo) {
                 return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
                     k_step<L, S, PAT_LOCAL, decltype(C)::value, decltype(Fo)::value, false,
@@ -256,7 +260,7 @@ cudaError_t launch_storage(const Launch &l)
     }
     if (l.kind == K_INIT) {
         return with_bool(l.pattern == 1, [&](auto AA) {
-            return with_model(l.model, [&](auto C) {
+            return with_model<S>(l.model, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
                     constexpr bool aa = decltype(AA)::value, fo = decltype(Fo)::value;
                     constexpr int c = decltype(C)::value;

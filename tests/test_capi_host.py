@@ -97,6 +97,16 @@ def test_create_validates_before_touching_memory(lib):
     o.trt_lambda = 3 / 16
     o.compressible = 1
     assert _create(lib, opts=o)[0] == lbm.LBM_ERR_ARG
+    # the compressible model runs with FP64 / FP32 storage
+    o = lbm.lbm_default_opts()
+    o.compressible = 1
+    for st, rc in ((lbm.LBM_F64, lbm.LBM_OK), (lbm.LBM_F32, lbm.LBM_OK),
+                   (lbm.LBM_F16S, lbm.LBM_ERR_ARG), (lbm.LBM_BF16S, lbm.LBM_ERR_ARG)):
+        o.storage = st
+        r, ctx = _create(lib, opts=o)
+        assert r == rc, st
+        if r == lbm.LBM_OK:
+            lib.lbm_destroy(ctx)
 
 
 def test_state_machine_errors_without_launch(lib):
