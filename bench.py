@@ -283,13 +283,15 @@ def run_config_lines(world, device):
 
     def timed(name, lat, steps, N):
         lat.step(8)
+        barrier(world)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         lat.step(steps)
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        barrier(world)
+        ms = max_over_ranks(e0.elapsed_time(e1), world, device)
         out[name] = {"glups": N * steps / (ms * 1e-3) / 1e9 * world, "ms": ms, "steps": steps,
                      "us_per_step": ms * 1e3 / steps}
 
