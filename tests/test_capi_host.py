@@ -142,3 +142,16 @@ def test_state_machine_errors_without_launch(lib):
     finally:
         lib.lbm_destroy(ctx)
     assert lib.lbm_step_count(None) == -1
+
+
+def test_noalloc_reduction_refuses_faces_and_obstacles(lib):
+    # Checked on the host before any device call (the pointers are never used).
+    out = (ctypes.c_double * 6)()
+    o = lbm.lbm_default_opts()
+    assert lib.lbm_reduce_state_noalloc(lbm.LBM_D3Q19, 8, 8, 8, lbm.LBM_BC_FACES,
+                                        ctypes.byref(o), ctypes.c_void_p(256), 0, None, None,
+                                        out) == lbm.LBM_ERR_ARG
+    o.geometry = 1
+    assert lib.lbm_reduce_state_noalloc(lbm.LBM_D3Q19, 8, 8, 8, lbm.LBM_BC_CAVITY,
+                                        ctypes.byref(o), ctypes.c_void_p(256), 0, None, None,
+                                        out) == lbm.LBM_ERR_ARG
