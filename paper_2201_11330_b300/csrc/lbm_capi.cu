@@ -179,6 +179,19 @@ void fill_lid_terms(lbm_ctx *c)
     }
 }
 
+template <class L>
+void fill_row_offsets(lbm_ctx *c)
+{
+    const long long N = c->N, sy = c->nx, sz = (long long)c->nx * c->ny;
+    for (int a = 0; a < kMaxQ; ++a)
+        c->sp.pull_off[a] = c->sp.push_off[a] = c->sp.push_st[a] = 0;
+    for (int a = 0; a < L::Q; ++a) {
+        const long long shift = L::e(a, 1) * sy + L::e(a, 2) * sz;
+        c->sp.pull_off[a] = a * N - shift;
+        c->sp.push_off[a] = c->sp.push_st[a] = a * N + shift;
+    }
+}
+
 void fill_params(lbm_ctx *c)
 {
     ++c->param_version;
@@ -242,6 +255,12 @@ void fill_params(lbm_ctx *c)
         fill_lid_terms<D3Q19>(c);
     else
         fill_lid_terms<D3Q27>(c);
+    if (c->lattice == LBM_D2Q9)
+        fill_row_offsets<D2Q9>(c);
+    else if (c->lattice == LBM_D3Q19)
+        fill_row_offsets<D3Q19>(c);
+    else
+        fill_row_offsets<D3Q27>(c);
     p.F = c->force;
     p.u_out = nullptr;
 }

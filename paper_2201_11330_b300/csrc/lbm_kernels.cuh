@@ -70,6 +70,15 @@ struct StepParams {
     double *partials;  // per-block monitor sums (RED kernels)
     const float *F;  // body force, d*N component-major (FORCE kernels)
     void *u_out;     // velocity output, d*N component-major, kernel arithmetic type (UOUT)
+    // Element offsets from node n, for rows with neighbours in y and z on both
+    // sides: pull_off[a] = slot a of the row shifted by -e_a (a N - e_a,y nx -
+    // e_a,z nx ny), push_off[a] = slot a of the row shifted by +e_a.  Uniform
+    // across the grid, so an access costs one add to the node's address.
+    long long pull_off[kMaxQ];
+    long long push_off[kMaxQ];
+    // push_off again, read by the AA push stores: a separate copy keeps the
+    // compiler from holding the loads' offsets in registers across the collision
+    long long push_st[kMaxQ];
 };
 
 template <class R>

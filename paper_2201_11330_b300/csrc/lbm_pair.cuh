@@ -289,6 +289,8 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
     auto word = [&](const unsigned short *base, size_t i) -> unsigned {
         return *reinterpret_cast<const unsigned *>(base + i);
     };
+    const unsigned short *src_n = src + n;
+    unsigned short *dst_n = dst + n;
 
     // ---- gather the incoming pairs -------------------------------------------
     // Phase 1 issues every load (aligned words, the warp-edge words, the
@@ -308,6 +310,23 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
         // slot `bs` of the node itself beyond a wall
         constexpr int ns = (PAT == PAT_PULL) ? a : b;
         constexpr int bs = (PAT == PAT_PULL) ? b : a;
+        if constexpr (IROW) {
+            // q: position x of slot ns in the row shifted by -e_a
+            const unsigned short *q = src_n + (PAT == PAT_PULL ? p.pull_off[a] : p.push_off[b]);
+            W[a] = active ? word(q, 0) : 0u;
+            if constexpr (ex == 1) {
+                if (active && x == 0)
+                    Wx[a] = xper ? q[nx - 1] : src_n[(size_t)bs * N];
+                else if (active && lane == 0)
+                    Wx[a] = *reinterpret_cast<const unsigned *>(q - 2);
+            } else if constexpr (ex == -1) {
+                if (active && x + 2 == nx)
+                    Wx[a] = xper ? q[-x] : src_n[(size_t)bs * N + 1];
+                else if (active && lane == 31)
+                    Wx[a] = word(q, 2);
+            }
+            return;
+        }
         bool yzw;
         const int srow = shifted_row<L, a, -1, IROW>(p, y, z, yzw);
         if (ex == 0 || yzw) {
@@ -415,6 +434,50 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
             return;
         }
         // AA push of f*_a to x + e_a (slot a); beyond a wall: slot b of the node
+        if constexpr (IROW) {
+            unsigned short *q = dst_n + p.push_st[a];  // position x of slot a, row shifted by +e_a
+            if constexpr (ex == 0) {
+                if (active)
+                    *reinterpret_cast<unsigned *>(q) = O;
+            } else if constexpr (ex == 1) {
+                // targets (x+1, x+2); this lane writes the aligned word (x+2, x+3)
+                const unsigned On = __shfl_down_sync(0xffffffffu, O, 1);
+                if (!active)
+                    return;
+                const bool last = lane == 31 || x + 2 >= nx;
+                if (lane == 0)
+                    q[1] = (unsigned short)lo16(O);
+                if (x + 2 < nx) {
+                    if (last)
+                        q[2] = (unsigned short)hi16(O);
+                    else
+                        *reinterpret_cast<unsigned *>(q + 2) = join_hi_lo(O, On);
+                } else if (xper) {
+                    q[-x] = (unsigned short)hi16(O);
+                } else {
+                    dst_n[(size_t)b * N + 1] = (unsigned short)hi16(O);
+                }
+            } else {
+                // targets (x-1, x); this lane writes the aligned word (x-2, x-1)
+                const unsigned Op = __shfl_up_sync(0xffffffffu, O, 1);
+                if (!active)
+                    return;
+                const bool last = lane == 31 || x + 2 >= nx;
+                if (x == 0) {
+                    if (xper)
+                        q[nx - 1] = (unsigned short)lo16(O);
+                    else
+                        dst_n[(size_t)b * N] = (unsigned short)lo16(O);
+                } else if (lane == 0) {
+                    q[-1] = (unsigned short)lo16(O);
+                } else {
+                    *reinterpret_cast<unsigned *>(q - 2) = join_hi_lo(Op, O);
+                }
+                if (last)
+                    q[0] = (unsigned short)hi16(O);
+            }
+            return;
+        }
         bool yzw;
         const int trow = shifted_row<L, a, +1, IROW>(p, y, z, yzw);
         if (ex == 0 || yzw) {
