@@ -434,14 +434,29 @@ __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typenam
         SFor<0, Q>::run([&](auto A_) {
             constexpr int a = decltype(A_)::value;
             constexpr int b = opp<L>(a);
-            int off;
-            bool wall;
-            upstream<L, a>(X, Y, Z, off, wall);
             const T *ptr;
-            if constexpr (PAT == PAT_PULL)
-                ptr = wall ? src + b * N + n : src + a * N + (n + off);
-            else
-                ptr = wall ? src + a * N + n : src + b * N + (n + off);
+            if constexpr (INTERIOR) {
+                // only x can wrap or meet a wall; y and z shifts are the
+                // uniform row offsets
+                constexpr int ex = L::e(a, 0);
+                const long long o = PAT == PAT_PULL ? p.pull_off[a] : p.push_off[b];
+                const T *s0 = src + n;
+                if constexpr (ex == 0) {
+                    ptr = s0 + o;
+                } else {
+                    const bool wall = ex == 1 ? X.wp : X.wm;
+                    const int xo = ex == 1 ? X.op : X.om;
+                    ptr = wall ? s0 + (size_t)(PAT == PAT_PULL ? b : a) * N : (s0 + xo) + o;
+                }
+            } else {
+                int off;
+                bool wall;
+                upstream<L, a>(X, Y, Z, off, wall);
+                if constexpr (PAT == PAT_PULL)
+                    ptr = wall ? src + b * N + n : src + a * N + (n + off);
+                else
+                    ptr = wall ? src + a * N + n : src + b * N + (n + off);
+            }
             R v;
             if constexpr (EARLY_RED)  // an idle lane reads nothing (the slots are owned)
                 v = active ? Sto<S>::dec(ld(ptr)) : R(0);
@@ -491,6 +506,18 @@ __device__ __forceinline__ void step_node(const typename Sto<S>::T *src, typenam
             st(dst + b * N + n, Sto<S>::enc(g[a]));
         } else {
             // push f*_a to x + e_a, whose upstream along -e_b is x
+            if constexpr (INTERIOR) {
+                constexpr int ex = L::e(a, 0);
+                T *d0 = dst + n;
+                if constexpr (ex == 0) {
+                    st(d0 + p.push_st[a], Sto<S>::enc(g[a]));
+                } else {
+                    const bool wall = ex == 1 ? X.wm : X.wp;
+                    const int xo = ex == 1 ? X.om : X.op;
+                    st(wall ? d0 + (size_t)b * N : (d0 + xo) + p.push_st[a], Sto<S>::enc(g[a]));
+                }
+                return;
+            }
             int off;
             bool wall;
             upstream<L, b>(X, Y, Z, off, wall);

@@ -76,6 +76,12 @@ inline cudaError_t with_model(int m, F &&f)
 // plain D3Q27 pull / gather kernels with 16-bit storage: blocks per SM bound
 template <class L, int S>
 constexpr int kPlainMinBlocks = (L::Q == 27 && (S == ST_F16S || S == ST_BF16S)) ? 5 : 0;
+// the AA gather half also with FP32 storage (three blocks: unbounded it takes
+// 97 registers, two blocks per SM)
+template <class L, int S>
+constexpr int kPlainGatherMinBlocks = kPlainMinBlocks<L, S> > 0 ? kPlainMinBlocks<L, S>
+                                      : (L::Q == 27 && S == ST_F32) ? 3
+                                                                    : 0;
 
 template <class L, int S>
 cudaError_t launch_storage(const Launch &l)
@@ -238,8 +244,8 @@ cudaError_t launch_storage(const Launch &l)
                     if (l.sp.partials != nullptr)
                         k_step_gather_red<L, S, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, dst,
                                                                                          l.sp);
-                    else if constexpr (kPlainMinBlocks<L, S> > 0)
-                        k_step_bounded<L, S, PAT_GATHER, c, fo, kPlainMinBlocks<L, S>>
+                    else if constexpr (kPlainGatherMinBlocks<L, S> > 0)
+                        k_step_bounded<L, S, PAT_GATHER, c, fo, kPlainGatherMinBlocks<L, S>>
                             <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
                     else
                         k_step<L, S, PAT_GATHER, c, fo, false, false>
