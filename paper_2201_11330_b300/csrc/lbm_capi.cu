@@ -5,6 +5,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -14,6 +15,11 @@
 #include "lbm_geo.cuh"
 #include "lbm_pair.cuh"
 #include "lbm_kernels.cuh"
+
+// bytes of every row next to an open x face that the node-list launch takes
+#ifndef LBM_XMARGIN_BYTES
+#define LBM_XMARGIN_BYTES 32
+#endif
 
 using namespace lbm;
 
@@ -208,6 +214,9 @@ void fill_params(lbm_ctx *c)
     p.nlist_len = 0;
     p.part_base = 0;
     p.open_faces = 0;
+    // An open x face's nodes lie one per row: the node list takes whole DRAM
+    // sectors of them (and the plain kernel leaves those sectors alone)
+    p.xm = std::max(1, LBM_XMARGIN_BYTES / (int)storage_elem(c->opts.storage));
     for (int i = 0; i < 6; ++i)
         if (c->face[i] == LBM_FACE_INLET || c->face[i] == LBM_FACE_OUTFLOW ||
             c->face[i] == LBM_FACE_SYMMETRY || c->face[i] == LBM_FACE_NODAL)

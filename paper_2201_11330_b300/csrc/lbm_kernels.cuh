@@ -67,6 +67,8 @@ struct StepParams {
     int nlist_len;          // entries of nlist
     long long part_base;    // node-list launches: first partial entry of their blocks
     int open_faces;         // bit f: face f is an inlet, outflow, symmetry or nodal face
+    int xm;                 // node-list launches: the first / last xm nodes of every row
+                            // next to an open x face go to the general kernel
     double *partials;  // per-block monitor sums (RED kernels)
     const float *F;  // body force, d*N component-major (FORCE kernels)
     void *u_out;     // velocity output, d*N component-major, kernel arithmetic type (UOUT)
@@ -629,7 +631,7 @@ __global__ void __launch_bounds__(256, 5) k_step_gather_red(const typename Sto<S
 __device__ __forceinline__ bool needs_general(const StepParams &p, int n, int x, int y, int z)
 {
     const int f = p.open_faces;
-    bool open = ((f & 1) && x == 0) || ((f & 2) && x == p.nx - 1) || ((f & 4) && y == 0) ||
+    bool open = ((f & 1) && x < p.xm) || ((f & 2) && x >= p.nx - p.xm) || ((f & 4) && y == 0) ||
                 ((f & 8) && y == p.ny - 1) || ((f & 16) && z == 0) || ((f & 32) && z == p.nz - 1);
     return open || (p.links && p.links[n] != 0u);
 }
