@@ -615,9 +615,17 @@ __global__ void __launch_bounds__(256, MINB) k_step_bounded(const typename Sto<S
 }
 
 // The AA gather half with the monitor fused in: held to five blocks per SM
-// (48 registers, a few bytes spilled) instead of the 62 it takes unbounded.
+// (48 registers, a few bytes spilled) instead of the 62 it takes unbounded;
+// D3Q19 FP32 without force to six (40 registers; measured at 512^3: 3.41 ms
+// at six, 3.68 at five, 3.86 at four, 4.42 at seven).  FP64 (three) and
+// D3Q27 (four) get more registers: at five they spill 100-1200 bytes.
+template <class L, int S, bool FORCE>
+constexpr int kGatherRedMinBlocks = S == ST_F64                          ? 3
+                                    : L::Q == 27                         ? 4
+                                    : (L::Q == 19 && S == ST_F32 && !FORCE) ? 6
+                                                                         : 5;
 template <class L, int S, int MODEL, bool FORCE>
-__global__ void __launch_bounds__(256, 5) k_step_gather_red(const typename Sto<S>::T *src,
+__global__ void __launch_bounds__(256, (kGatherRedMinBlocks<L, S, FORCE>)) k_step_gather_red(const typename Sto<S>::T *src,
                                                             typename Sto<S>::T *dst,
                                                             const StepParams p)
 {
