@@ -389,3 +389,29 @@ def test_paired_and_plain_bulk_agree_with_faces_and_obstacles(storage):
     # same link terms, summed in other block groupings (FP32 partial sums)
     assert np.allclose(outs[0][2], outs[1][2], rtol=2e-5, atol=1e-9)
     assert abs(outs[0][3] - outs[1][3]) < 1e-6 * nx * ny * nz
+
+
+# The node list takes the first / last 32 bytes of every row next to an open x
+# face (4 FP64, 8 FP32, 16 FP16 nodes); row lengths below, at and above twice
+# that, so that rows are wholly listed, split, or mostly plain.
+@pytest.mark.parametrize("storage,nx", [("f64", 3), ("f64", 8), ("f64", 9), ("f64", 17),
+                                        ("f32", 15), ("f32", 16), ("f32", 17), ("f32", 41),
+                                        ("f16s", 16), ("f16s", 32), ("f16s", 34),
+                                        ("f16s", 66), ("f16s", 33)])
+def test_open_x_faces_for_row_lengths_around_the_list_margin(storage, nx):
+    ny, nz = 6, 5
+    p0, u0 = W.random_smooth_state(nx, ny, nz, 3, amp_u=0.03, amp_p=2e-3, seed=50 + nx)
+    sol = np.zeros((nz, ny, nx), np.uint8)
+    sol[1:3, 2:4, nx // 2] = 1
+    u0[:, sol.ravel() != 0] = 0
+    inl = np.zeros((3, ny * nz))
+    inl[0] = 0.04
+    got, ref = run_pair("d3q19", (nx, ny, nz), 0.7,
+                        ["inlet", "outflow", "wall", "wall", "periodic", "periodic"], 23,
+                        storage=storage, solid=sol, inlet=inl, lid=(0.05, 0.0, 0.0), p0=p0,
+                        u0=u0, force_out=True)
+    eu, ep = field_errors(got, ref, 0.05)
+    assert eu < TOL_U[storage] and ep < 10 * TOL_U[storage], (eu, ep)
+    fscale = np.abs(ref[2]).max()
+    tol_f = {"f64": 1e-12, "f32": 1e-4, "f16s": 3e-2}[storage]
+    assert np.abs(got[2] - ref[2]).max() < tol_f * fscale
