@@ -170,7 +170,7 @@ size_t lbm_workspace_bytes(int lattice, int nx, int ny, int nz, const lbm_opts *
  * (workspace too small).  LBM_BC_FACES and obstacles run the pull scheme:
  * the plain (16-bit storage: paired) kernel on the nodes that touch only
  * walls, the lid and periodic faces, and the general kernel, one node per
- * thread, on a list of the rest; the staged variant is not available. */
+ * thread, on a list of the rest. */
 int lbm_create(int lattice, int nx, int ny, int nz, double tau, int bc, const lbm_opts *opts,
                void *dev_workspace, size_t bytes, void *cuda_stream, lbm_ctx **out);
 
@@ -242,29 +242,22 @@ int64_t lbm_step_count(const lbm_ctx *ctx);
 /* Which kernel runs the step (all compute the same arithmetic and give
  * bitwise identical results):
  *   LBM_KERNEL_PLAIN  one node per thread, Q populations straight from HBM;
- *   LBM_KERNEL_STAGED persistent blocks stage whole row segments of every
- *                     direction in shared memory with bulk asynchronous copies
- *                     (cp.async.bulk + mbarrier, several segments in flight);
- *                     needs nx to be a multiple of 16 bytes' worth of values
- *                     (8 for 16-bit storage, 4 for FP32, 2 for FP64) and the
- *                     incompressible BGK model;
  *   LBM_KERNEL_PAIRED 16-bit storage only, nx even: two adjacent nodes per
  *                     thread, one 32-bit word per slot, e_x = +-1 directions
  *                     realigned with warp shuffles;
  *   LBM_KERNEL_AUTO   the library's measured choice for the storage type
  *                     (PAIRED where eligible, else PLAIN).
  * The adjoint's recompute always uses the plain kernel.  LBM_ERR_ARG for an
- * unknown variant or STAGED on an ineligible shape.  A bounded wait of the
- * staged kernel that times out is reported by the next lbm_reduce as
- * LBM_ERR_CUDA. */
+ * unknown variant (2 is not used: it numbered a shared-memory staged
+ * variant that measured slower than PLAIN everywhere and was removed) or
+ * PAIRED on an ineligible context. */
 typedef enum {
     LBM_KERNEL_AUTO = 0,
     LBM_KERNEL_PLAIN = 1,
-    LBM_KERNEL_STAGED = 2,
     LBM_KERNEL_PAIRED = 3
 } lbm_kernel_variant;
 int lbm_set_kernel_variant(lbm_ctx *ctx, int variant);
-/* The variant lbm_step currently launches (PLAIN, STAGED or PAIRED). */
+/* The variant lbm_step currently launches (PLAIN or PAIRED). */
 int lbm_kernel_variant_in_use(const lbm_ctx *ctx);
 
 /* lbm_step(n) whose last step also computes the Monitor values of

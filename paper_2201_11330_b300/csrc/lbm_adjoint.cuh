@@ -72,7 +72,13 @@ __device__ __forceinline__ void adjoint_node(const StepParams &p, const AdjParam
     R s = R(0), v[3] = {R(0), R(0), R(0)}, w[3] = {R(0), R(0), R(0)}, zz[3] = {R(0), R(0), R(0)};
     SFor<0, Q>::run([&](auto A_) {
         constexpr int a = decltype(A_)::value;
-        const R tm = R(L::w(a)) * mu[a];
+        // FP32: the weight as hi + lo (see w_lo), or the momentum mode of the
+        // adjoint grows by 1 + 7.45e-9 omega per reverse step
+        R tm;
+        if constexpr (std::is_same<R, float>::value)
+            tm = wmul<L, a>(mu[a]);
+        else
+            tm = R(L::w(a)) * mu[a];
         s += tm;
         R eu = R(0), eF = R(0);
         (void)eF;
@@ -90,6 +96,7 @@ __device__ __forceinline__ void adjoint_node(const StepParams &p, const AdjParam
         });
         const R tmu = tm * eu;
         R tmf = R(0);
+        (void)tmf;
         if constexpr (FORCE)
             tmf = tm * eF;
         SFor<0, 3>::run([&](auto K_) {

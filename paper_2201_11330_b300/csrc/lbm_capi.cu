@@ -10,7 +10,6 @@
 #include <vector>
 
 #include "lbm.h"
-#include "lbm_bulk.cuh"
 #include "lbm_capi_internal.h"
 #include "lbm_geo.cuh"
 #include "lbm_pair.cuh"
@@ -277,24 +276,10 @@ void fill_params(lbm_ctx *c)
 // p.inlet survives fill_params (which lbm_set_lid calls)
 void keep_inlet(lbm_ctx *c, const float *inlet) { c->sp.inlet = inlet; }
 
-// The staged kernel copies whole 16-byte aligned row segments: nx (hence N)
-// must be a multiple of 16 bytes' worth of values.
-bool bulk_eligible(const lbm_ctx *c)
-{
-    const int per16 = 16 / (int)storage_elem(c->opts.storage);
-    const bool bgk_inc = !c->opts.compressible && c->opts.collision == LBM_COLL_BGK;
-    return bgk_inc && c->nx % per16 == 0;
-}
-
 // The paired kernel moves two 16-bit values per thread and slot.
 bool pair_eligible(const lbm_ctx *c)
 {
     return (c->opts.storage == LBM_F16S || c->opts.storage == LBM_BF16S) && c->nx % 2 == 0;
-}
-
-bool use_bulk(const lbm_ctx *c)
-{
-    return c->kernel_variant == LBM_KERNEL_STAGED && bulk_eligible(c);
 }
 
 bool use_pair(const lbm_ctx *c, int pattern = PAT_PULL)
@@ -433,19 +418,6 @@ int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u
         if (reduce_blocks)
             *reduce_blocks = (long long)((c->nx + 2 * kPairThreads - 1) / (2 * kPairThreads)) *
                              c->ny * c->nz;
-    } else if (use_bulk(c) && !reduce_blocks) {
-        if (c->num_sms <= 0) {
-            int dev = 0, nsm = 0;
-            if (cudaGetDevice(&dev) != cudaSuccess ||
-                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-                return LBM_ERR_CUDA;
-            c->num_sms = nsm;
-        }
-        l.bulk = true;
-        l.bulk_xseg = (c->nx + kBulkSeg - 1) / kBulkSeg;
-        l.bulk_nseg = l.bulk_xseg * c->ny * c->nz;
-        l.num_sms = c->num_sms;
-        l.err = c->err;
     }
     if (reduce_blocks && !l.pair)
         *reduce_blocks = (long long)l.grid.x * l.grid.y * l.grid.z;
@@ -570,8 +542,6 @@ int lbm_create(int lattice, int nx, int ny, int nz, double tau, int bc, const lb
     c->bx = default_block(nx);
     c->initialized = false;
     c->kernel_variant = LBM_KERNEL_AUTO;
-    c->num_sms = 0;
-    c->err = (unsigned *)((char *)c->result + 64);
     c->geo = geo;
     for (int i = 0; i < 6; ++i)
         c->face[i] = face[i];
@@ -610,8 +580,6 @@ int init_from(lbm_ctx *c, const void *p, const void *u, bool in_f32)
     c->cur = 0;
     l.dst = c->f[0];
     c->step = 0;
-    if (cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream) != cudaSuccess)
-        return LBM_ERR_CUDA;
     if (dispatch(c->lattice, l) != cudaSuccess)
         return LBM_ERR_CUDA;
     c->initialized = true;
@@ -830,13 +798,10 @@ int64_t lbm_step_count(const lbm_ctx *c) { return c ? c->step : -1; }
 
 int lbm_set_kernel_variant(lbm_ctx *c, int variant)
 {
-    if (!c || variant < LBM_KERNEL_AUTO || variant > LBM_KERNEL_PAIRED)
-        return LBM_ERR_ARG;
-    if (variant == LBM_KERNEL_STAGED && !bulk_eligible(c))
+    if (!c || (variant != LBM_KERNEL_AUTO && variant != LBM_KERNEL_PLAIN &&
+               variant != LBM_KERNEL_PAIRED))
         return LBM_ERR_ARG;
     if (variant == LBM_KERNEL_PAIRED && !pair_eligible(c))
-        return LBM_ERR_ARG;
-    if (c->geo && variant == LBM_KERNEL_STAGED)
         return LBM_ERR_ARG;
     c->kernel_variant = variant;
     ++c->param_version;
@@ -847,9 +812,7 @@ int lbm_kernel_variant_in_use(const lbm_ctx *c)
 {
     if (!c)
         return LBM_ERR_ARG;
-    if (c->geo)
-        return use_pair(c) ? LBM_KERNEL_PAIRED : LBM_KERNEL_PLAIN;
-    return use_pair(c) ? LBM_KERNEL_PAIRED : use_bulk(c) ? LBM_KERNEL_STAGED : LBM_KERNEL_PLAIN;
+    return use_pair(c) ? LBM_KERNEL_PAIRED : LBM_KERNEL_PLAIN;
 }
 
 int lbm_step_reduce(lbm_ctx *c, int64_t n, double *out)
@@ -878,14 +841,10 @@ int lbm_step_reduce(lbm_ctx *c, int64_t n, double *out)
         return LBM_ERR_CUDA;
     if (launch_finish(c->partials, nout, c->result, c->stream) != cudaSuccess)
         return LBM_ERR_CUDA;
-    double r[12];
+    double r[kReduceVals];
     if (cudaMemcpyAsync(r, c->result, sizeof(r), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
         return LBM_ERR_CUDA;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess)
-        return LBM_ERR_CUDA;
-    unsigned errword;
-    memcpy(&errword, (const char *)r + 64, sizeof(errword));
-    if (errword != 0)
         return LBM_ERR_CUDA;
     out[0] = r[0] + (c->shifted ? (double)c->n_fluid : 0.0);
     for (int k = 1; k < 5; ++k)
@@ -956,15 +915,11 @@ int lbm_reduce(lbm_ctx *c, double *out)
         return rc;
     if (launch_finish(c->partials, c->nred, c->result, c->stream) != cudaSuccess)
         return LBM_ERR_CUDA;
-    double r[12];  // the six values, padding, the error word at byte 64
+    double r[kReduceVals];
     if (cudaMemcpyAsync(r, c->result, sizeof(r), cudaMemcpyDeviceToHost, c->stream) !=
         cudaSuccess)
         return LBM_ERR_CUDA;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess)
-        return LBM_ERR_CUDA;
-    unsigned errword;
-    memcpy(&errword, (const char *)r + 64, sizeof(errword));
-    if (errword != 0)
         return LBM_ERR_CUDA;
     out[0] = r[0] + (c->shifted ? (double)c->n_fluid : 0.0);
     out[1] = r[1];

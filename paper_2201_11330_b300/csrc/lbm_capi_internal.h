@@ -32,8 +32,6 @@ struct lbm_ctx {
     int bx;  // threads per block along x
     bool initialized;
     int kernel_variant;  // lbm_kernel_variant
-    int num_sms;         // queried at the first staged launch
-    unsigned *err;       // error word of the bounded waits (in the workspace)
     // per-face boundaries and obstacles (the general step kernel)
     bool geo;                   // LBM_BC_FACES or obstacles
     int face[6];                // lbm_face per face

@@ -117,7 +117,7 @@ __device__ __forceinline__ void st(T *p, T v)
 }
 
 // ---- explicitly rounded arithmetic ------------------------------------------
-// The collision is inlined into several kernels (pull, AA halves, staged); to
+// The collision is inlined into several kernels (pull, AA halves, paired); to
 // make all of them round identically, every multiply-add is written out: the
 // _rn intrinsics are never fused or split by the compiler.
 __device__ __forceinline__ float o_add(float a, float b) { return __fadd_rn(a, b); }
@@ -138,6 +138,17 @@ __device__ __forceinline__ double o_fma(double a, double b, double c) { return _
 // equilibrium as kf*S_a, and opposite directions are handled in pairs:
 //   feq_a = t_a [A + 4.5 rho (e.u)^2] +/- t_a 3 rho (e.u),
 //   A = sum g - 1.5 rho u.u  (the sigma*t_a shift cancels).
+// x t_a for the odd (momentum) part of the equilibrium: in FP32 with the
+// weight split into hi + lo (see w_lo), in FP64 a plain product.
+template <class L, int a, class R>
+__device__ __forceinline__ R wmul(R x)
+{
+    if constexpr (std::is_same<R, float>::value)
+        return o_fma(x, w_hi<L>(a), o_mul(x, w_lo<L>(a)));
+    else
+        return o_mul(x, R(L::w(a)));
+}
+
 template <class L, class R, int MODEL, bool FORCE>
 __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coef<R> &c,
                                         R (&u)[3], R &s_out, R &rho_out)
@@ -232,7 +243,11 @@ __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coe
             pair_eq(A_, sym, asym);
             const R hp = o_mul(sp[a], R(0.5)), hm = o_mul(sm[a], R(0.5));
             const R gp = o_fma(om, o_fma(sym, t, -hp), hp);
-            const R gm = o_fma(omm, o_fma(asym, t, -hm), hm);
+            R gm;
+            if constexpr (std::is_same<R, float>::value)
+                gm = o_fma(omm, o_sub(wmul<L, a>(asym), hm), hm);
+            else
+                gm = o_fma(omm, o_fma(asym, t, -hm), hm);
             g[a] = o_add(gp, gm);
             g[b] = o_sub(gp, gm);
         });
@@ -246,7 +261,7 @@ __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coe
             // no product feeds an add directly: each multiply-add is one
             // explicit fma, so no compiler can fuse (and re-round) it
             // differently
-            const R at = o_mul(asym, t);
+            const R at = wmul<L, a>(asym);
             const R fa = o_fma(sym, t, at), fb = o_fma(sym, t, -at);
             g[a] = o_fma(om, o_sub(fa, g[a]), g[a]);
             g[b] = o_fma(om, o_sub(fb, g[b]), g[b]);
@@ -988,7 +1003,6 @@ struct Launch {
     MomParams mp;
     AdjParams ap;
     size_t count;  // K_FLUSH
-    bool bulk;     // K_STEP: use the shared-memory staged kernel (lbm_bulk.cuh)
     bool pair;     // K_STEP: two nodes per thread, 32-bit accesses (lbm_pair.cuh)
     bool geo;      // K_STEP: the general kernel (per-face boundaries, obstacles; lbm_geo.cuh)
     bool skip;     // K_STEP: the plain pull kernel on the nodes it can update (k_step_skip)
@@ -997,8 +1011,6 @@ struct Launch {
     const unsigned char *solid;  // K_LINKS: N bytes, nonzero = solid
     unsigned *links;             // K_LINKS: output link words
     unsigned long long *nsolid;  // K_LINKS: number of solid nodes (added to)
-    int bulk_nseg, bulk_xseg, num_sms;
-    unsigned *err;  // error word for bounded waits
     dim3 grid, block;
     cudaStream_t stream;
 };

@@ -3,45 +3,11 @@
 #pragma once
 
 #include "lbm_adjoint.cuh"
-#include "lbm_bulk.cuh"
 #include "lbm_geo.cuh"
 #include "lbm_kernels.cuh"
 #include "lbm_pair.cuh"
 
 namespace lbm {
-
-// Persistent launch of the staged kernel: as many blocks as fit on the GPU
-// (queried once per instantiation), never more than there are segments.
-template <class L, int S, int PAT, int MODEL, bool FORCE>
-cudaError_t launch_bulk(const Launch &l)
-{
-    using T = typename Sto<S>::T;
-    auto kern = k_step_bulk<L, S, PAT, MODEL, FORCE>;
-    constexpr size_t smem = bulk_smem_bytes<L, T>();
-    static int per_sm = -1;
-    if (per_sm < 0) {
-        cudaError_t e =
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        int b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kBulkSeg, smem);
-        if (e != cudaSuccess)
-            return e;
-        if (b < 1)
-            return cudaErrorInvalidConfiguration;
-        per_sm = b;
-    }
-    BulkParams bp;
-    bp.nseg = l.bulk_nseg;
-    bp.xseg = l.bulk_xseg;
-    bp.err = l.err;
-    int blocks = per_sm * (l.num_sms > 0 ? l.num_sms : 1);
-    if (blocks > bp.nseg)
-        blocks = bp.nseg;
-    kern<<<blocks, kBulkSeg, smem, l.stream>>>((const T *)l.src, (T *)l.dst, l.sp, bp);
-    return cudaGetLastError();
-}
 
 template <class F>
 inline cudaError_t with_bool(bool b, F &&f)
@@ -197,18 +163,6 @@ cudaError_t launch_storage(const Launch &l)
         } else {
             return cudaErrorInvalidValue;
         }
-    }
-    if (l.kind == K_STEP && l.bulk) {  // the staged variant: incompressible BGK only
-        if (l.model != M_INC)
-            return cudaErrorInvalidValue;
-        return with_bool(l.force, [&](auto Fo) {
-            constexpr bool fo = decltype(Fo)::value;
-            if (l.pattern == PAT_PULL)
-                return launch_bulk<L, S, PAT_PULL, M_INC, fo>(l);
-            if (l.pattern == PAT_GATHER)
-                return launch_bulk<L, S, PAT_GATHER, M_INC, fo>(l);
-            return launch_bulk<L, S, PAT_LOCAL, M_INC, fo>(l);
-        });
     }
     if (l.kind == K_STEP) {
         if (l.pattern == PAT_PULL) {

@@ -162,7 +162,8 @@ __device__ __forceinline__ void collide2(float2 (&g)[L::Q], const float2 (&F)[3]
             pair_eq(A_, sym, asym);
             const float2 hp = v_mul(sp[a], v_bc(0.5f)), hm = v_mul(sm[a], v_bc(0.5f));
             const float2 gp = v_fma(om, v_fma(sym, t, v_neg(hp)), hp);
-            const float2 gm = v_fma(omm, v_fma(asym, t, v_neg(hm)), hm);
+            const float2 at = v_fma(asym, t, v_mul(asym, v_bc(w_lo<L>(a))));
+            const float2 gm = v_fma(omm, v_sub(at, hm), hm);
             g[a] = v_add(gp, gm);
             g[b] = v_sub(gp, gm);
         });
@@ -173,7 +174,7 @@ __device__ __forceinline__ void collide2(float2 (&g)[L::Q], const float2 (&F)[3]
             const float2 t = v_bc(float(L::w(a)));
             float2 sym, asym;
             pair_eq(A_, sym, asym);
-            const float2 at = v_mul(asym, t);
+            const float2 at = v_fma(asym, t, v_mul(asym, v_bc(w_lo<L>(a))));
             const float2 fa = v_fma(sym, t, at), fb = v_fma(sym, t, v_neg(at));
             g[a] = v_fma(om, v_sub(fa, g[a]), g[a]);
             g[b] = v_fma(om, v_sub(fb, g[b]), g[b]);

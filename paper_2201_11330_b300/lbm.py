@@ -28,8 +28,8 @@ FACES = {"periodic": LBM_FACE_PERIODIC, "wall": LBM_FACE_WALL, "inlet": LBM_FACE
          "outflow": LBM_FACE_OUTFLOW, "symmetry": LBM_FACE_SYMMETRY, "nodal": LBM_FACE_NODAL}
 LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = 0, 1, 2, 3
 LBM_COLL_BGK, LBM_COLL_TRT = 0, 1
-LBM_KERNEL_AUTO, LBM_KERNEL_PLAIN, LBM_KERNEL_STAGED, LBM_KERNEL_PAIRED = 0, 1, 2, 3
-KERNELS = {"auto": LBM_KERNEL_AUTO, "plain": LBM_KERNEL_PLAIN, "staged": LBM_KERNEL_STAGED,
+LBM_KERNEL_AUTO, LBM_KERNEL_PLAIN, LBM_KERNEL_PAIRED = 0, 1, 3
+KERNELS = {"auto": LBM_KERNEL_AUTO, "plain": LBM_KERNEL_PLAIN,
            "paired": LBM_KERNEL_PAIRED}
 
 LATTICES = {"d2q9": LBM_D2Q9, "d3q19": LBM_D3Q19, "d3q27": LBM_D3Q27}
@@ -447,15 +447,14 @@ class Lattice:
         return lbm_step_count(self.ctx)
 
     def set_kernel(self, variant):
-        """'auto', 'plain', 'staged' or 'paired' (see lbm_set_kernel_variant)."""
+        """'auto', 'plain' or 'paired' (see lbm_set_kernel_variant)."""
         lbm_set_kernel_variant(self.ctx, _key(KERNELS, variant))
         return self
 
     @property
     def kernel(self):
         v = lbm_kernel_variant_in_use(self.ctx)
-        return {LBM_KERNEL_PLAIN: "plain", LBM_KERNEL_STAGED: "staged",
-                LBM_KERNEL_PAIRED: "paired"}[v]
+        return {LBM_KERNEL_PLAIN: "plain", LBM_KERNEL_PAIRED: "paired"}[v]
 
     def macroscopic(self, dtype=None):
         """(p (N,), u (d, N)) of the current step."""

@@ -260,8 +260,10 @@ def test_geometry_argument_checks():
     with pytest.raises(LBMError):  # geometry invalidates the state
         lat.step(1)
     lat.init()
-    with pytest.raises(LBMError):  # no staged variant with faces or obstacles
-        lat.set_kernel("staged")
+    with pytest.raises(LBMError):  # 2: no such variant
+        lat.set_kernel(2)
+    with pytest.raises(LBMError):  # paired needs 16-bit storage
+        lat.set_kernel("paired")
     assert lat.kernel == "plain"
     lat16 = Lattice("d3q19", 8, 8, 8, 0.6, "cavity", storage="f16s", obstacles=True)
     assert lat16.kernel == "paired"
