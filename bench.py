@@ -315,11 +315,13 @@ def run_config_lines(world, device):
     return out
 
 
-def run_e2e(n, re, storage, steps, warmup, world, device):
-    """Public API with host buffers: pinned-host FP32 initial fields ->
-    device, lbm_init_f32, then per step lbm_step_reduce (the step with the Monitor fused
-    in; 48 B to host), final macroscopic fields -> pinned host.  All inside
-    the timed region."""
+def run_e2e(n, re, storage, steps, warmup, world, device, per_step_monitor=True):
+    """Public API with host buffers, all inside the timed region: pinned-host
+    FP32 initial fields -> device, lbm_init_f32, the steps, final FP32
+    macroscopic fields -> pinned host.  per_step_monitor: every step is
+    lbm_step_reduce(1) (the step with the Monitor fused in; 48 B to the host
+    and a stream sync per step); else one lbm_step(steps) call and one
+    lbm_reduce at the end."""
     import torch
     from paper_2201_11330_b300 import workloads as W
     from paper_2201_11330_b300.lbm import Lattice
@@ -334,13 +336,18 @@ def run_e2e(n, re, storage, steps, warmup, world, device):
     u_dev = torch.empty((3, N), dtype=torch.float32, device=device)
     p_o = torch.empty((N,), dtype=torch.float32, device=device)
     u_o = torch.empty((3, N), dtype=torch.float32, device=device)
+    monitor = {}
 
     def job(nsteps):
         p_dev.copy_(p_host, non_blocking=True)
         u_dev.copy_(u_host, non_blocking=True)
         lat.init(p_dev, u_dev)
-        for _ in range(nsteps):
-            lat.step_reduce(1)
+        if per_step_monitor:
+            for _ in range(nsteps):
+                monitor.update(lat.step_reduce(1))
+        else:
+            lat.step(nsteps)
+            monitor.update(lat.reduce())
         lat.macroscopic_into(p_o, u_o)
         p_out.copy_(p_o, non_blocking=True)
         u_out.copy_(u_o, non_blocking=True)
@@ -355,12 +362,15 @@ def run_e2e(n, re, storage, steps, warmup, world, device):
     dt = max_over_ranks(time.perf_counter() - t0, world, device)
     h2d = (p_host.numel() + u_host.numel()) * 4
     d2h = (p_out.numel() + u_out.numel()) * 4
+    mon_bytes = 48 * (steps if per_step_monitor else 1)
+    how = ("per step lbm_step_reduce(1) (the step with the FP64 monitor fused in, 48 B to "
+           "host and a stream sync per step)" if per_step_monitor else
+           f"one lbm_step({steps}) call, then one lbm_reduce (48 B to host)")
     res = {"value": world * N * steps / dt / 1e9, "unit": "GLUPS",
-           "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": 48 + d2h / steps,
-           "steps": steps,
+           "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": (mon_bytes + d2h) / steps,
+           "steps": steps, "max_speed": monitor.get("max_speed"),
            "what": f"D3Q19 cavity {n}^3 {storage} AA via paper_2201_11330_b300.lbm.Lattice: "
-                   "pinned-host FP32 initial (p, u) -> device, lbm_init_f32, per step "
-                   "lbm_step_reduce(1) (step with the FP64 monitor fused in, 48 B to host), "
+                   f"pinned-host FP32 initial (p, u) -> device, lbm_init_f32, {how}, "
                    "final FP32 (p, u) -> pinned host"}
     del lat
     torch.cuda.empty_cache()
@@ -490,10 +500,15 @@ def main():
                     help="cavity side of the headline run (profiling uses smaller boxes)")
     ap.add_argument("--storage", default=HEADLINE["storage"], choices=list(BYTES_OF),
                     help="storage of the headline run (profiling of the other variants)")
+    ap.add_argument("--lattice", default=HEADLINE["lattice"], choices=["d3q19", "d3q27"],
+                    help="lattice of the headline run (profiling of the D3Q27 kernels)")
+    ap.add_argument("--pull", action="store_true",
+                    help="two-lattice pull scheme for the headline run (profiling)")
     ap.add_argument("--workload", default="cavity", choices=["cavity", "sphere"],
                     help="sphere: only the paper's D3Q27 sphere flow at --storage (profiling)")
     ap.add_argument("--no-extras", action="store_true",
-                    help="headline line only (no storage variants, D3Q27, adjoint, CPU)")
+                    help="headline line only, for profiling (no storage variants, D3Q27, "
+                         "adjoint, end-to-end legs, CPU)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.warmup < 3:
@@ -524,6 +539,10 @@ def main():
     hb = dict(HEADLINE)
     hb["n"] = args.size
     hb["storage"] = args.storage
+    hb["lattice"] = args.lattice
+    hb["aa"] = not args.pull
+    if args.lattice == "d3q27":  # the D3Q27 cavity is quoted at Re 2000
+        hb["re"] = 2000.0
     peak, peak_kind = load_peaks()
 
     # headline, with clocks sampled during its timed region
@@ -535,17 +554,24 @@ def main():
 
     N = head["nodes"]
     bpn = head["bytes_per_node"]
-    dom_ms = max(head["gather_ms"], head["local_ms"])
     st_tag = hb["storage"].upper()
-    gather_dom = head["gather_ms"] >= head["local_ms"]
-    dom_name = f"k_step<D3Q19,{st_tag},{'GATHER' if gather_dom else 'LOCAL'}>"
+    lat_tag = hb["lattice"].upper()
+    if hb["aa"]:
+        dom_ms = max(head["gather_ms"], head["local_ms"])
+        gather_dom = head["gather_ms"] >= head["local_ms"]
+        pat = "GATHER" if gather_dom else "LOCAL"
+    else:
+        dom_ms = head["pull_ms"]
+        pat = "PULL"
+    dom_name = f"k_step<{lat_tag},{st_tag},{pat}>"
     achieved = N * bpn / (dom_ms * 1e-3) / 1e9
-    traffic = load_traffic(f"d3q19_{hb['storage']}_{'gather' if gather_dom else 'local'}_{hb['n']}")
+    traffic = load_traffic(f"{hb['lattice']}_{hb['storage']}_{pat.lower()}_{hb['n']}")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": dom_name, "peak_kind": f"{peak_kind} copy bandwidth",
                 "algorithmic_bytes_per_launch": N * bpn,
-                "gather_ms": head["gather_ms"], "local_ms": head["local_ms"],
+                "gather_ms": head.get("gather_ms"), "local_ms": head.get("local_ms"),
+                "pull_ms": head.get("pull_ms"),
                 "frac_of_8TBs": N * bpn / (dom_ms * 1e-3) / 8e12}
 
     extras = {}
@@ -578,8 +604,15 @@ def main():
             extras["adjoint"] = run_adjoint(128, 2000, 100, world, device)
         except Exception as exc:  # reported, not hidden
             extras["adjoint"] = {"error": str(exc)}
-    e2e = run_e2e(hb["n"], hb["re"], hb["storage"], max(10, args.steps // 2), args.warmup,
-                  world, device)
+    # end to end through the public API: the contract's per-step metric read,
+    # and the stepping call with one monitor read at the end; at least 100
+    # steps so that the one-off host copies do not swamp the steps
+    e2e = e2e_step_n = None
+    if not args.no_extras:
+        e2e_steps = max(100, args.steps)
+        e2e = run_e2e(hb["n"], hb["re"], hb["storage"], e2e_steps, args.warmup, world, device)
+        e2e_step_n = run_e2e(hb["n"], hb["re"], hb["storage"], e2e_steps, args.warmup, world,
+                             device, per_step_monitor=False)
 
     cpu = cpu_baseline_sample() if (rank == 0 and world == 1 and not args.no_extras) else None
 
@@ -597,6 +630,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "e2e_step_n": e2e_step_n,
             "gpu_launches": args.steps,
             "clocks": clocks,
             "mass_rel_drift": head["mass_rel_drift"],

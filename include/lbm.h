@@ -317,15 +317,18 @@ int lbm_adjoint(lbm_ctx *ctx, int64_t T, int64_t K, void *adj_workspace, size_t 
  * Scratch: a fixed device array inside the library holding
  * LBM_NOALLOC_MAX_PARTIALS partial sums (8 doubles each) plus the result,
  * about 512 KB, present on every GPU that loads the library until the
- * process exits.  The call needs ceil(nx/256) * nz partials (x-segments of
- * at most 256 nodes times z-planes) and returns LBM_ERR_NOMEM, launching
- * nothing, when that exceeds LBM_NOALLOC_MAX_PARTIALS.  Every partial is
- * rewritten by each call, so nothing needs clearing; but all calls on a
- * device share the array, so calls that overlap on the GPU (different
- * streams or threads) race and must be serialised by the caller.  The
- * first call on each device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture.
+ * process exits.  The call needs at least ceil(nx/256) * nz partials
+ * (x-segments of at most 256 nodes times z-planes; the rows of each are
+ * split over further blocks as far as the array allows) and returns
+ * LBM_ERR_NOMEM, launching nothing, when that exceeds
+ * LBM_NOALLOC_MAX_PARTIALS.  Every partial a call uses is rewritten by it,
+ * so nothing needs clearing; but all calls on a device share the array, so
+ * calls that overlap on the GPU (different streams or threads) race and must
+ * be serialised by the caller.  Every call looks up the array's device
+ * address on the current device with cudaGetSymbolAddress (so the address is
+ * never stale, even after a device reset); the first call on a device also
+ * loads the library's device code there, so make it before any stream
+ * capture.
  *
  * Arguments: lattice, nx, ny, nz, bc and *opts as given to lbm_create for
  * the context that produced the buffer (one of the three named box types,

@@ -318,6 +318,8 @@ Launch base_launch(const lbm_ctx *c, int kind)
 // ---- internal helpers shared with the adjoint driver ------------------------
 namespace lbm {
 
+bool ctx_opts_valid(const lbm_opts &o) { return valid_opts(o); }
+
 Launch ctx_base_launch(const lbm_ctx *c, int kind) { return base_launch(c, kind); }
 
 // Lists the nodes the plain kernel cannot update (solid, obstacle links,

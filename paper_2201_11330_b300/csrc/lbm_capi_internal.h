@@ -60,6 +60,8 @@ struct lbm_ctx {
 };
 
 namespace lbm {
+// lbm_opts that lbm_create accepts (the option checks, without the shape)
+bool ctx_opts_valid(const lbm_opts &o);
 lbm::Launch ctx_base_launch(const lbm_ctx *c, int kind);
 cudaError_t ctx_dispatch(const lbm_ctx *c, const lbm::Launch &l);
 int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u_out,

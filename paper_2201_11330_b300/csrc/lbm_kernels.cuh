@@ -771,6 +771,72 @@ __device__ __forceinline__ R warp_max(R v)
     return v;
 }
 
+// Node n's moments from a stored state in form FORM: s = sum of the stored
+// populations (the shifted pressure sum), rho, and u = (j* - F/2)/rho from
+// the post-collision momentum j* = j + F.  Shared by every kernel that
+// reduces or outputs the moments of a state, so that they agree bit for bit.
+template <class L, int S, int FORM, bool COMP, bool FORCE>
+__device__ __forceinline__ void node_moments(const typename Sto<S>::T *src, const StepParams &p,
+                                             int x, int y, int z, int n,
+                                             typename Sto<S>::R &s, typename Sto<S>::R &rho,
+                                             typename Sto<S>::R (&u)[3])
+{
+    using R = typename Sto<S>::R;
+    constexpr int Q = L::Q;
+    const Coef<R> &c = coef<R>(p);
+    const size_t N = (size_t)p.N;
+    R g[Q];
+    if constexpr (FORM == FORM_LOCAL) {
+        SFor<0, Q>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            g[a] = Sto<S>::dec(src[a * N + n]);
+        });
+    } else if constexpr (FORM == FORM_SWAPPED) {
+        SFor<0, Q>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            g[a] = Sto<S>::dec(src[opp<L>(a) * N + n]);
+        });
+    } else {
+        AxisNbr X, Y, Z;
+        make_axes<L, false>(p, x, y, z, X, Y, Z);
+        SFor<0, Q>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            constexpr int b = opp<L>(a);
+            int off;
+            bool wall;
+            upstream<L, b>(X, Y, Z, off, wall);
+            if (wall) {
+                g[a] = Sto<S>::dec(src[b * N + n]);
+            } else {
+                g[a] = Sto<S>::dec(src[a * N + (n + off)]);
+            }
+        });
+    }
+    R j[3] = {R(0), R(0), R(0)};
+    s = R(0);
+    SFor<0, Q>::run([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        s = o_add(s, g[a]);
+        SFor<0, 3>::run([&](auto K_) {
+            constexpr int k = decltype(K_)::value;
+            if constexpr (L::e(a, k) == 1)
+                j[k] = o_add(j[k], g[a]);
+            else if constexpr (L::e(a, k) == -1)
+                j[k] = o_sub(j[k], g[a]);
+        });
+    });
+    rho = COMP ? o_add(s, c.sigma) : c.rho0;
+    const R ir = COMP ? R(1) / rho : c.inv_rho0;
+    for (int k = 0; k < 3; ++k) {
+        R jk = j[k];
+        if constexpr (FORCE) {
+            if (k < L::D)
+                jk = o_fma(R(-0.5), R(p.F[k * N + n]), jk);
+        }
+        u[k] = o_mul(jk, ir);
+    }
+}
+
 // Grid-stride over x-segments of rows; each block keeps FP64 partial sums of
 // the per-node values (reduced across a warp in the kernel's arithmetic
 // first) and writes them to partials[blockIdx.x].
@@ -778,9 +844,7 @@ template <class L, int S, int FORM, bool COMP, bool FORCE>
 __global__ void __launch_bounds__(256) k_moments(const typename Sto<S>::T *src, const StepParams p,
                                                  const MomParams m)
 {
-    using T = typename Sto<S>::T;
     using R = typename Sto<S>::R;
-    constexpr int Q = L::Q;
     const Coef<R> &c = coef<R>(p);
     const size_t N = (size_t)p.N;
     double acc[kReduceVals] = {0, 0, 0, 0, 0, 0};
@@ -811,60 +875,10 @@ __global__ void __launch_bounds__(256) k_moments(const typename Sto<S>::T *src, 
         }
         if (x < p.nx && !solid) {
             const int n = n0;
-            R g[Q];
-            if constexpr (FORM == FORM_LOCAL) {
-                SFor<0, Q>::run([&](auto A_) {
-                    constexpr int a = decltype(A_)::value;
-                    g[a] = Sto<S>::dec(src[a * N + n]);
-                });
-            } else if constexpr (FORM == FORM_SWAPPED) {
-                SFor<0, Q>::run([&](auto A_) {
-                    constexpr int a = decltype(A_)::value;
-                    g[a] = Sto<S>::dec(src[opp<L>(a) * N + n]);
-                });
-            } else {
-                AxisNbr X, Y, Z;
-                make_axes<L, false>(p, x, y, z, X, Y, Z);
-                SFor<0, Q>::run([&](auto A_) {
-                    constexpr int a = decltype(A_)::value;
-                    constexpr int b = opp<L>(a);
-                    int off;
-                    bool wall;
-                    upstream<L, b>(X, Y, Z, off, wall);
-                    if (wall) {
-                        g[a] = Sto<S>::dec(src[b * N + n]);
-                    } else {
-                        g[a] = Sto<S>::dec(src[a * N + (n + off)]);
-                    }
-                });
-            }
-            R s = R(0), j[3] = {R(0), R(0), R(0)};
-            SFor<0, Q>::run([&](auto A_) {
-                constexpr int a = decltype(A_)::value;
-                s = o_add(s, g[a]);
-                SFor<0, 3>::run([&](auto K_) {
-                    constexpr int k = decltype(K_)::value;
-                    if constexpr (L::e(a, k) == 1)
-                        j[k] = o_add(j[k], g[a]);
-                    else if constexpr (L::e(a, k) == -1)
-                        j[k] = o_sub(j[k], g[a]);
-                });
-            });
-            // post-collision state: j* = j + F, so u = (j* - F/2)/rho
-            const R rho = COMP ? o_add(s, c.sigma) : c.rho0;
-            const R ir = COMP ? R(1) / rho : c.inv_rho0;
-            R u[3];
-            for (int k = 0; k < 3; ++k) {
-                R jk = j[k];
-                if constexpr (FORCE) {
-                    if (k < L::D)
-                        jk = o_fma(R(-0.5), R(p.F[k * N + n]), jk);
-                }
-                u[k] = o_mul(jk, ir);
-            }
-            const R uu = o_fma(u[2], u[2], o_fma(u[1], u[1], o_mul(u[0], u[0])));
+            R s_, rho, u[3];
+            node_moments<L, S, FORM, COMP, FORCE>(src, p, x, y, z, n, s_, rho, u);
             if (m.p_out) {
-                const R pv = (s + c.sigma) * R(1.0 / 3.0);
+                const R pv = (s_ + c.sigma) * R(1.0 / 3.0);
                 if (m.out_f32)
                     ((float *)m.p_out)[n] = float(pv);
                 else
@@ -878,12 +892,7 @@ __global__ void __launch_bounds__(256) k_moments(const typename Sto<S>::T *src, 
                         ((double *)m.u_out)[k * N + n] = double(u[k]);
                 }
             }
-            vals[0] = s;
-            vals[1] = rho * u[0];
-            vals[2] = rho * u[1];
-            vals[3] = rho * u[2];
-            vals[4] = R(0.5) * rho * uu;
-            vals[5] = uu;
+            monitor_values(s_, rho, u, vals);
         }
         if (m.partials) {
 #pragma unroll

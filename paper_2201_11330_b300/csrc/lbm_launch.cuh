@@ -66,34 +66,28 @@ cudaError_t launch_storage(const Launch &l)
                     auto *d16 = (unsigned short *)l.dst;
                     return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
                         constexpr bool rd = decltype(Rd)::value;
-                        // measured: D3Q27 pull and gather at six blocks per SM,
-                        // D3Q19 pull at eight (its gather is issue-bound and
-                        // spills when bounded)
-                        constexpr int minb = L::Q == 27 ? 6 : L::Q == 19 ? 8 : 0;
-                        if constexpr (minb > 0 && !rd) {
-                            if (l.pattern == PAT_PULL)
-                                k_step_pair_bounded<L, S, PAT_PULL, c, fo, minb>
-                                    <<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
-                            else if (l.pattern == PAT_GATHER && L::Q == 27)
-                                k_step_pair_bounded<L, S, PAT_GATHER, c, fo, minb>
-                                    <<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
-                            else if (l.pattern == PAT_GATHER)
-                                k_step_pair<L, S, PAT_GATHER, c, fo, rd>
+                        // blocks per SM of each paired kernel (0: unbounded),
+                        // measured on B300 (512^3 D3Q19, 768^3 D3Q27 cavities)
+                        constexpr int mb_pull = L::Q == 27 ? 7 : L::Q == 19 ? 8 : 0;
+                        constexpr int mb_gather = L::Q == 27 ? 6 : L::Q == 19 ? 8 : 0;
+                        constexpr int mb_local = L::Q == 19 ? 8 : 0;
+                        auto go = [&](auto P, auto MB) {
+                            constexpr int pt = decltype(P)::value, m = decltype(MB)::value;
+                            if constexpr (m > 0 && !rd)
+                                k_step_pair_bounded<L, S, pt, c, fo, m>
                                     <<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
                             else
-                                k_step_pair<L, S, PAT_LOCAL, c, fo, rd>
+                                k_step_pair<L, S, pt, c, fo, rd>
                                     <<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
-                        } else {
-                            if (l.pattern == PAT_PULL)
-                                k_step_pair<L, S, PAT_PULL, c, fo, rd>
-                                    <<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
-                            else if (l.pattern == PAT_GATHER)
-                                k_step_pair<L, S, PAT_GATHER, c, fo, rd>
-                                    <<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
-                            else
-                                k_step_pair<L, S, PAT_LOCAL, c, fo, rd>
-                                    <<<grid, kPairThreads, 0, l.stream>>>(s16, d16, l.sp);
-                        }
+                        };
+                        using std::integral_constant;
+                        if (l.pattern == PAT_PULL)
+                            go(integral_constant<int, PAT_PULL>{}, integral_constant<int, mb_pull>{});
+                        else if (l.pattern == PAT_GATHER)
+                            go(integral_constant<int, PAT_GATHER>{},
+                               integral_constant<int, mb_gather>{});
+                        else
+                            go(integral_constant<int, PAT_LOCAL>{}, integral_constant<int, mb_local>{});
                         return cudaGetLastError();
                     });
                 });

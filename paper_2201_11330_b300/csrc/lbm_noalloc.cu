@@ -11,11 +11,12 @@
 // is a file-scope device array of fixed size that every GPU loading the
 // library holds until the process exits.
 #include <math.h>
+#include <algorithm>
 #include <string.h>
 
-#include <mutex>
 
 #include "lbm.h"
+#include "lbm_capi_internal.h"
 #include "lbm_kernels.cuh"
 
 using namespace lbm;
@@ -23,110 +24,47 @@ using namespace lbm;
 namespace {
 
 constexpr int kStaticPartials = LBM_NOALLOC_MAX_PARTIALS;
-constexpr int kMaxDevices = 64;
 
-// One partial (kPartialStride doubles) per (x-segment, z-plane) block, then
-// the 6-double result.  Shared by every call on a device.
+// One partial (kPartialStride doubles) per block, then the 6-double result.
+// Shared by every call on a device.
 static __device__ __align__(256) double g_noalloc_scratch[kStaticPartials * kPartialStride + 8];
 
-std::mutex g_setup_mutex;
-double *g_scratch_ptr[kMaxDevices];
-
 // Device address of the scratch array on the current device.  In host code
-// g_noalloc_scratch is only a stand-in symbol, so the address is looked up
-// once per device, with that device current.
+// g_noalloc_scratch is only a stand-in symbol; the address is looked up on
+// every call (cheap once the module is loaded), so it is never stale, even
+// after the device's primary context was reset.
 cudaError_t scratch_for_current_device(double **out)
 {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess)
         return e;
-    if (dev < 0 || dev >= kMaxDevices)
-        return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess)
-            return e;
-        g_scratch_ptr[dev] = (double *)p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = (double *)p;
     return cudaSuccess;
 }
 
-// grid (xseg, nz): block (xs, z) walks every row y of its z-plane segment and
-// writes one FP64 partial; the per-node arithmetic is that of k_moments.
+// grid (xseg, nz, ychunks): block (xs, z, c) walks the rows y = c, c +
+// ychunks, ... of its z-plane segment and writes one FP64 partial.  The
+// per-node values are those of k_moments (node_moments, monitor_values),
+// bit for bit, and so are the warp sums of a row segment; only the order in
+// which the FP64 partials are added differs.
 template <class L, int S, int FORM, bool COMP, bool FORCE>
 __global__ void __launch_bounds__(256) k_moments_noalloc(const typename Sto<S>::T *src,
                                                          const StepParams p, double *partials,
                                                          int xseg)
 {
     using R = typename Sto<S>::R;
-    constexpr int Q = L::Q;
-    const Coef<R> &c = coef<R>(p);
-    const size_t N = (size_t)p.N;
-    const int xs = blockIdx.x, z = blockIdx.y;
+    const int xs = blockIdx.x, z = blockIdx.y, c0 = blockIdx.z;
     const int x = xs * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     double acc[kReduceVals] = {0, 0, 0, 0, 0, 0};
-    for (int y = 0; y < p.ny; ++y) {
+    for (int y = c0; y < p.ny; y += gridDim.z) {
         R vals[kReduceVals] = {R(0), R(0), R(0), R(0), R(0), R(0)};
         if (x < p.nx) {
             const int n = x + p.nx * (y + p.ny * z);
-            R g[Q];
-            if constexpr (FORM == FORM_LOCAL) {
-                SFor<0, Q>::run([&](auto A_) {
-                    constexpr int a = decltype(A_)::value;
-                    g[a] = Sto<S>::dec(src[a * N + n]);
-                });
-            } else if constexpr (FORM == FORM_SWAPPED) {
-                SFor<0, Q>::run([&](auto A_) {
-                    constexpr int a = decltype(A_)::value;
-                    g[a] = Sto<S>::dec(src[opp<L>(a) * N + n]);
-                });
-            } else {
-                AxisNbr X, Y, Z;
-                make_axes<L, false>(p, x, y, z, X, Y, Z);
-                SFor<0, Q>::run([&](auto A_) {
-                    constexpr int a = decltype(A_)::value;
-                    constexpr int b = opp<L>(a);
-                    int off;
-                    bool wall;
-                    upstream<L, b>(X, Y, Z, off, wall);
-                    g[a] = wall ? Sto<S>::dec(src[b * N + n]) : Sto<S>::dec(src[a * N + (n + off)]);
-                });
-            }
-            R s = R(0), j[3] = {R(0), R(0), R(0)};
-            SFor<0, Q>::run([&](auto A_) {
-                constexpr int a = decltype(A_)::value;
-                s += g[a];
-                SFor<0, 3>::run([&](auto K_) {
-                    constexpr int k = decltype(K_)::value;
-                    if constexpr (L::e(a, k) == 1)
-                        j[k] += g[a];
-                    else if constexpr (L::e(a, k) == -1)
-                        j[k] -= g[a];
-                });
-            });
-            const R rho = COMP ? s + c.sigma : c.rho0;
-            const R ir = COMP ? R(1) / rho : c.inv_rho0;
-            R u[3];
-            for (int k = 0; k < 3; ++k) {
-                R jk = j[k];
-                if constexpr (FORCE) {
-                    if (k < L::D)
-                        jk -= R(0.5) * R(p.F[k * N + n]);
-                }
-                u[k] = jk * ir;
-            }
-            const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-            vals[0] = s;
-            vals[1] = rho * u[0];
-            vals[2] = rho * u[1];
-            vals[3] = rho * u[2];
-            vals[4] = R(0.5) * rho * uu;
-            vals[5] = uu;
+            R s, rho, u[3];
+            node_moments<L, S, FORM, COMP, FORCE>(src, p, x, y, z, n, s, rho, u);
+            monitor_values(s, rho, u, vals);
         }
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -149,7 +87,8 @@ __global__ void __launch_bounds__(256) k_moments_noalloc(const typename Sto<S>::
         double r = sh[0][k];
         for (int w = 1; w < nwarps; ++w)
             r = (k == 5) ? fmax(r, sh[w][k]) : r + sh[w][k];
-        partials[((size_t)z * xseg + xs) * kPartialStride + k] = r;  // every slot rewritten
+        const size_t b = ((size_t)c0 * gridDim.y + z) * xseg + xs;
+        partials[b * kPartialStride + k] = r;  // every slot of the launch rewritten
     }
 }
 
@@ -165,9 +104,11 @@ cudaError_t launch_s(const void *state, int form, bool comp, bool force, const S
 {
     using T = typename Sto<S>::T;
     const T *src = (const T *)state;
-    return pick(comp, [&](auto C) {
+    // the compressible model runs with FP64 / FP32 storage only
+    constexpr bool wide = S == ST_F64 || S == ST_F32;
+    return pick(comp && wide, [&](auto C) {
         return pick(force, [&](auto Fo) {
-            constexpr bool c = decltype(C)::value, fo = decltype(Fo)::value;
+            constexpr bool c = decltype(C)::value && wide, fo = decltype(Fo)::value;
             if (form == FORM_LOCAL)
                 k_moments_noalloc<L, S, FORM_LOCAL, c, fo><<<grid, block, 0, st>>>(src, p, partials, xseg);
             else if (form == FORM_SWAPPED)
@@ -211,17 +152,19 @@ extern "C" int lbm_reduce_state_noalloc(int lattice, int nx, int ny, int nz, int
     if ((long long)nx * ny * nz >= (1LL << 31))
         return LBM_ERR_ARG;
     const lbm_opts &o = *opts;
-    if (o.storage < LBM_F64 || o.storage > LBM_BF16S || !(o.rho0 > 0.0) || !isfinite(o.rho0))
+    if (!ctx_opts_valid(o))  // the options lbm_create accepts
         return LBM_ERR_ARG;
     if (o.geometry)  // solid nodes are known only to a context
         return LBM_ERR_ARG;
-    // same launch shape as the context path: x-segments of up to 256 nodes
+    // same row segments as the context path: x-segments of up to 256 nodes
     int bx = (nx + 31) / 32 * 32;
     if (bx > 256)
         bx = 256;
     const int xseg = (nx + bx - 1) / bx;
     if ((long long)xseg * nz > kStaticPartials)
         return LBM_ERR_NOMEM;  // the fixed scratch holds LBM_NOALLOC_MAX_PARTIALS partials
+    // rows of a z-plane segment split over blocks, as far as the scratch allows
+    const int ychunks = (int)std::min<long long>(ny, kStaticPartials / ((long long)xseg * nz));
     double *scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess)
         return LBM_ERR_CUDA;
@@ -247,7 +190,7 @@ extern "C" int lbm_reduce_state_noalloc(int lattice, int nx, int ny, int nz, int
     p.F = force;
     const int form = !o.aa ? FORM_LOCAL : (step % 2 == 0 ? FORM_SWAPPED : FORM_STREAMED);
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const dim3 grid(xseg, nz, 1), block(bx, 1, 1);
+    const dim3 grid(xseg, nz, ychunks), block(bx, 1, 1);
     cudaError_t e;
     switch (lattice) {
     case LBM_D2Q9:
@@ -265,7 +208,7 @@ extern "C" int lbm_reduce_state_noalloc(int lattice, int nx, int ny, int nz, int
     }
     if (e != cudaSuccess)
         return LBM_ERR_CUDA;
-    k_reduce_finish<<<1, 256, 0, st>>>(partials, xseg * nz, result);
+    k_reduce_finish<<<1, 256, 0, st>>>(partials, xseg * nz * ychunks, result);
     if (cudaGetLastError() != cudaSuccess)
         return LBM_ERR_CUDA;
     double r[kReduceVals];

@@ -73,31 +73,79 @@ __device__ __forceinline__ float2 v_fma(float2 a, float2 b, float2 c)
 __device__ __forceinline__ float2 v_bc(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float2 v_neg(float2 a) { return make_float2(-a.x, -a.y); }
 
-// collide() of lbm_kernels.cuh on two nodes at once, operation for operation.
-template <class L, int MODEL, bool FORCE>
-__device__ __forceinline__ void collide2(float2 (&g)[L::Q], const float2 (&F)[3],
-                                         const Coef<float> &c, float2 (&u_out)[3], float2 &s_out,
-                                         float2 &rho_out)
+template <int S>
+__device__ __forceinline__ float2 dec2(unsigned w);
+template <>
+__device__ __forceinline__ float2 dec2<ST_F16S>(unsigned w)
+{
+    __half2 h;
+    memcpy(&h, &w, 4);
+    return __half22float2(h);
+}
+template <>
+__device__ __forceinline__ float2 dec2<ST_BF16S>(unsigned w)
+{
+    __nv_bfloat162 h;
+    memcpy(&h, &w, 4);
+    return __bfloat1622float2(h);
+}
+template <int S>
+__device__ __forceinline__ unsigned enc2(float2 v);
+template <>
+__device__ __forceinline__ unsigned enc2<ST_F16S>(float2 v)
+{
+    const __half2 h = __float22half2_rn(v);
+    unsigned w;
+    memcpy(&w, &h, 4);
+    return w;
+}
+template <>
+__device__ __forceinline__ unsigned enc2<ST_BF16S>(float2 v)
+{
+    const __nv_bfloat162 h = __float22bfloat162_rn(v);
+    unsigned w;
+    memcpy(&w, &h, 4);
+    return w;
+}
+
+// collide() of lbm_kernels.cuh on two nodes at once, operation for operation,
+// on the stored words: W[a] holds the two nodes' 16-bit values of direction
+// a and is rewritten with the post-collision values.  The populations are
+// kept packed (one register per direction instead of two) and decoded again
+// where they are used: decoding is exact, so the results are those of
+// collide() bit for bit, with about Q registers fewer live through the moment
+// pass.  `top`: the pair lies on the row next to the moving wall, whose e_y =
+// -1 populations carry the lid term (added at every decode, as the scalar
+// kernel adds it once).
+template <class L, int S, int MODEL, bool FORCE>
+__device__ __forceinline__ void collide2w(unsigned (&W)[L::Q], bool top, const float2 (&F)[3],
+                                          const Coef<float> &c, float2 (&u_out)[3],
+                                          float2 &s_out, float2 &rho_out)
 {
     constexpr bool COMP = MODEL == M_COMP;
     constexpr int H = L::Q / 2;
-    float2 sp[H], sm[H];
-    SFor<0, H>::run([&](auto A_) {
+    auto g = [&](auto A_) -> float2 {
         constexpr int a = decltype(A_)::value;
-        sp[a] = v_add(g[a], g[opp<L>(a)]);
-        sm[a] = v_sub(g[a], g[opp<L>(a)]);
-    });
-    float2 s = g[H];
+        float2 v = dec2<S>(W[a]);
+        if constexpr (L::e(a, 1) == -1) {
+            if (top)
+                v = v_add(v, v_bc(c.lid[a]));
+        }
+        return v;
+    };
+    float2 s = g(std::integral_constant<int, H>{});
     float2 j[3] = {v_bc(0.f), v_bc(0.f), v_bc(0.f)};
     SFor<0, H>::run([&](auto A_) {
         constexpr int a = decltype(A_)::value;
-        s = v_add(s, sp[a]);
+        const float2 ga = g(A_), gb = g(std::integral_constant<int, opp<L>(a)>{});
+        const float2 sp = v_add(ga, gb), sm = v_sub(ga, gb);
+        s = v_add(s, sp);
         SFor<0, 3>::run([&](auto K_) {
             constexpr int k = decltype(K_)::value;
             if constexpr (L::e(a, k) == 1)
-                j[k] = v_add(j[k], sm[a]);
+                j[k] = v_add(j[k], sm);
             else if constexpr (L::e(a, k) == -1)
-                j[k] = v_sub(j[k], sm[a]);
+                j[k] = v_sub(j[k], sm);
         });
     });
     float2 rho, ir;
@@ -160,12 +208,14 @@ __device__ __forceinline__ void collide2(float2 (&g)[L::Q], const float2 (&F)[3]
             const float2 t = v_bc(float(L::w(a)));
             float2 sym, asym;
             pair_eq(A_, sym, asym);
-            const float2 hp = v_mul(sp[a], v_bc(0.5f)), hm = v_mul(sm[a], v_bc(0.5f));
+            const float2 ga = g(A_), gb = g(std::integral_constant<int, b>{});
+            const float2 hp = v_mul(v_add(ga, gb), v_bc(0.5f));
+            const float2 hm = v_mul(v_sub(ga, gb), v_bc(0.5f));
             const float2 gp = v_fma(om, v_fma(sym, t, v_neg(hp)), hp);
             const float2 at = v_fma(asym, t, v_mul(asym, v_bc(w_lo<L>(a))));
             const float2 gm = v_fma(omm, v_sub(at, hm), hm);
-            g[a] = v_add(gp, gm);
-            g[b] = v_sub(gp, gm);
+            W[a] = enc2<S>(v_add(gp, gm));
+            W[b] = enc2<S>(v_sub(gp, gm));
         });
     } else {
         SFor<0, H>::run([&](auto A_) {
@@ -176,52 +226,19 @@ __device__ __forceinline__ void collide2(float2 (&g)[L::Q], const float2 (&F)[3]
             pair_eq(A_, sym, asym);
             const float2 at = v_fma(asym, t, v_mul(asym, v_bc(w_lo<L>(a))));
             const float2 fa = v_fma(sym, t, at), fb = v_fma(sym, t, v_neg(at));
-            g[a] = v_fma(om, v_sub(fa, g[a]), g[a]);
-            g[b] = v_fma(om, v_sub(fb, g[b]), g[b]);
+            const float2 ga = g(A_), gb = g(std::integral_constant<int, b>{});
+            W[a] = enc2<S>(v_fma(om, v_sub(fa, ga), ga));
+            W[b] = enc2<S>(v_fma(om, v_sub(fb, gb), gb));
         });
     }
     {
         const float2 t0 = v_bc(float(L::w(H)));
-        g[H] = v_fma(om, v_fma(t0, A, v_neg(g[H])), g[H]);
+        const float2 gH = g(std::integral_constant<int, H>{});
+        W[H] = enc2<S>(v_fma(om, v_fma(t0, A, v_neg(gH)), gH));
     }
     u_out[0] = u[0];
     u_out[1] = u[1];
     u_out[2] = u[2];
-}
-
-template <int S>
-__device__ __forceinline__ float2 dec2(unsigned w);
-template <>
-__device__ __forceinline__ float2 dec2<ST_F16S>(unsigned w)
-{
-    __half2 h;
-    memcpy(&h, &w, 4);
-    return __half22float2(h);
-}
-template <>
-__device__ __forceinline__ float2 dec2<ST_BF16S>(unsigned w)
-{
-    __nv_bfloat162 h;
-    memcpy(&h, &w, 4);
-    return __bfloat1622float2(h);
-}
-template <int S>
-__device__ __forceinline__ unsigned enc2(float2 v);
-template <>
-__device__ __forceinline__ unsigned enc2<ST_F16S>(float2 v)
-{
-    const __half2 h = __float22half2_rn(v);
-    unsigned w;
-    memcpy(&w, &h, 4);
-    return w;
-}
-template <>
-__device__ __forceinline__ unsigned enc2<ST_BF16S>(float2 v)
-{
-    const __nv_bfloat162 h = __float22bfloat162_rn(v);
-    unsigned w;
-    memcpy(&w, &h, 4);
-    return w;
 }
 
 constexpr int kPairThreads = 128;  // threads per block; 256 nodes per block
@@ -281,6 +298,20 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
     const bool xper = p.periodic & 1;
     const bool top = p.lid_on && (y == p.ny - 1);
     bool own = active;  // this pair is collided and stored here
+    // interior rows: the warp-edge cases as per-thread predicates, fixed for
+    // the whole step; the row ends (x = 0, x + 2 = nx: at most two warps of a
+    // row) are fixed up behind one warp-uniform flag in the AA push stores
+    // Two forms of the interior rows' loads, bitwise identical: the row ends
+    // as per-lane conditions inside each direction, or fixed up behind a
+    // warp-uniform flag (measured faster for the D3Q19 AA gather only).
+    constexpr bool kUniformRowEnd = L::Q == 19 && PAT == PAT_GATHER;
+    const bool first = x == 0, last_pair = x + 2 == nx;
+    const bool row_end = __any_sync(0xffffffffu, first || last_pair);
+    const bool ld_xp = active && lane == 0 && !first;       // e_x = +1: word before the warp
+    const bool ld_xm = active && lane == 31 && !last_pair;  // e_x = -1: word after the warp
+    (void)row_end;
+    (void)ld_xp;
+    (void)ld_xm;
     if constexpr (SKIP) {
         static_assert(PAT == PAT_PULL, "the pull scheme only");
         if (active)
@@ -311,6 +342,21 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
         // slot `bs` of the node itself beyond a wall
         constexpr int ns = (PAT == PAT_PULL) ? a : b;
         constexpr int bs = (PAT == PAT_PULL) ? b : a;
+        if constexpr (IROW && kUniformRowEnd) {
+            // q: position x of slot ns in the row shifted by -e_a; lane 0 (31)
+            // also loads the word before (after) the warp's span for e_x = +1 (-1)
+            const unsigned short *q = src_n + (PAT == PAT_PULL ? p.pull_off[a] : p.push_off[b]);
+            if (active)
+                W[a] = word(q, 0);
+            if constexpr (ex == 1) {
+                if (ld_xp)
+                    Wx[a] = *reinterpret_cast<const unsigned *>(q - 2);
+            } else if constexpr (ex == -1) {
+                if (ld_xm)
+                    Wx[a] = word(q, 2);
+            }
+            return;
+        }
         if constexpr (IROW) {
             // q: position x of slot ns in the row shifted by -e_a
             const unsigned short *q = src_n + (PAT == PAT_PULL ? p.pull_off[a] : p.push_off[b]);
@@ -349,7 +395,35 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
                 Wx[a] = word(rbase, x + 2);
         }
     });
-    if constexpr (PAT != PAT_LOCAL) {
+    if constexpr (PAT != PAT_LOCAL && IROW && kUniformRowEnd) {
+        SFor<0, Q>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            constexpr int b = opp<L>(a);
+            constexpr int ex = L::e(a, 0);
+            constexpr int bs = (PAT == PAT_PULL) ? b : a;
+            if constexpr (ex == 1) {
+                // positions (x-1, x): hi of the previous word, lo of W
+                const unsigned wp = __shfl_up_sync(0xffffffffu, W[a], 1);
+                W[a] = join_hi_lo(lane == 0 ? Wx[a] : wp, W[a]);
+                if (row_end && first) {  // position -1: periodic image or wall (own slot bs)
+                    const unsigned short *q =
+                        src_n + (PAT == PAT_PULL ? p.pull_off[a] : p.push_off[b]);
+                    const unsigned e = xper ? q[nx - 1] : src_n[(size_t)bs * N];
+                    W[a] = (W[a] & 0xffff0000u) | e;
+                }
+            } else if constexpr (ex == -1) {
+                // positions (x+1, x+2): hi of W, lo of the next word
+                const unsigned wn = __shfl_down_sync(0xffffffffu, W[a], 1);
+                W[a] = join_hi_lo(W[a], lane == 31 ? Wx[a] : wn);
+                if (row_end && last_pair) {  // position nx: periodic image or wall
+                    const unsigned short *q =
+                        src_n + (PAT == PAT_PULL ? p.pull_off[a] : p.push_off[b]);
+                    const unsigned e = xper ? q[-x] : src_n[(size_t)bs * N + 1];
+                    W[a] = (W[a] & 0x0000ffffu) | (e << 16);
+                }
+            }
+        });
+    } else if constexpr (PAT != PAT_LOCAL) {
         SFor<0, Q>::run([&](auto A_) {
             constexpr int a = decltype(A_)::value;
             constexpr int ex = L::e(a, 0);
@@ -385,27 +459,13 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
     float mon[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     // ---- collide nodes x and x+1 together (packed FP32) ------------------------
     if (own) {
-        float2 g[Q];
-        SFor<0, Q>::run([&](auto A_) {
-            constexpr int a = decltype(A_)::value;
-            float2 v = dec2<S>(W[a]);
-            if constexpr (L::e(a, 1) == -1) {
-                if (top)
-                    v = make_float2(v.x + c.lid[a], v.y + c.lid[a]);
-            }
-            g[a] = v;
-        });
         float2 F[3] = {v_bc(0.f), v_bc(0.f), v_bc(0.f)};
         if constexpr (FORCE) {
             for (int k = 0; k < L::D; ++k)
                 F[k] = *reinterpret_cast<const float2 *>(p.F + k * N + n);
         }
         float2 u2[3], s2, rho2;
-        collide2<L, MODEL, FORCE>(g, F, c, u2, s2, rho2);
-        SFor<0, Q>::run([&](auto A_) {
-            constexpr int a = decltype(A_)::value;
-            W[a] = enc2<S>(g[a]);
-        });
+        collide2w<L, S, MODEL, FORCE>(W, top, F, c, u2, s2, rho2);
         if constexpr (RED) {  // the two nodes' monitor values, summed in the thread
             float m0[6], m1[6];
             const float ua[3] = {u2[0].x, u2[1].x, u2[2].x}, ub[3] = {u2[0].y, u2[1].y, u2[2].y};
@@ -436,46 +496,45 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
         }
         // AA push of f*_a to x + e_a (slot a); beyond a wall: slot b of the node
         if constexpr (IROW) {
-            unsigned short *q = dst_n + p.push_st[a];  // position x of slot a, row shifted by +e_a
+            // q: position x of slot a in the row shifted by +e_a
+            unsigned short *q = dst_n + p.push_st[a];
             if constexpr (ex == 0) {
                 if (active)
                     *reinterpret_cast<unsigned *>(q) = O;
             } else if constexpr (ex == 1) {
-                // targets (x+1, x+2); this lane writes the aligned word (x+2, x+3)
+                // targets (x+1, x+2): the aligned word (x+2, x+3) takes this
+                // lane's hi and the next lane's lo; lane 0 writes x+1 alone, lane
+                // 31 x+2 alone; the row's last pair pushes x+2 = nx beyond the end
                 const unsigned On = __shfl_down_sync(0xffffffffu, O, 1);
-                if (!active)
-                    return;
-                const bool last = lane == 31 || x + 2 >= nx;
-                if (lane == 0)
+                if (active && lane != 31 && !last_pair)
+                    *reinterpret_cast<unsigned *>(q + 2) = join_hi_lo(O, On);
+                if (active && lane == 0)
                     q[1] = (unsigned short)lo16(O);
-                if (x + 2 < nx) {
-                    if (last)
-                        q[2] = (unsigned short)hi16(O);
+                if (ld_xm)
+                    q[2] = (unsigned short)hi16(O);
+                if (row_end && active && last_pair) {
+                    if (xper)
+                        q[-x] = (unsigned short)hi16(O);
                     else
-                        *reinterpret_cast<unsigned *>(q + 2) = join_hi_lo(O, On);
-                } else if (xper) {
-                    q[-x] = (unsigned short)hi16(O);
-                } else {
-                    dst_n[(size_t)b * N + 1] = (unsigned short)hi16(O);
+                        dst_n[(size_t)b * N + 1] = (unsigned short)hi16(O);
                 }
             } else {
-                // targets (x-1, x); this lane writes the aligned word (x-2, x-1)
+                // targets (x-1, x): the aligned word (x-2, x-1) takes the
+                // previous lane's hi and this lane's lo; lane 0 writes x-1 alone
+                // (x = 0: beyond the row start), the warp's or row's last pair x
                 const unsigned Op = __shfl_up_sync(0xffffffffu, O, 1);
-                if (!active)
-                    return;
-                const bool last = lane == 31 || x + 2 >= nx;
-                if (x == 0) {
+                if (active && lane != 0)
+                    *reinterpret_cast<unsigned *>(q - 2) = join_hi_lo(Op, O);
+                if (ld_xp)
+                    q[-1] = (unsigned short)lo16(O);
+                if (active && (lane == 31 || last_pair))
+                    q[0] = (unsigned short)hi16(O);
+                if (row_end && active && first) {
                     if (xper)
                         q[nx - 1] = (unsigned short)lo16(O);
                     else
                         dst_n[(size_t)b * N] = (unsigned short)lo16(O);
-                } else if (lane == 0) {
-                    q[-1] = (unsigned short)lo16(O);
-                } else {
-                    *reinterpret_cast<unsigned *>(q - 2) = join_hi_lo(Op, O);
                 }
-                if (last)
-                    q[0] = (unsigned short)hi16(O);
             }
             return;
         }
@@ -551,10 +610,9 @@ __global__ void __launch_bounds__(kPairThreads, 6) k_step_pair_skip(const unsign
         pair_body<L, S, PAT_PULL, MODEL, FORCE, false, MON == 1, true>(src, dst, p);
 }
 
-// Pull (and for D3Q27 the AA gather) held to MINB blocks per SM: D3Q27 six
-// (90-94 -> 80 registers), D3Q19 eight (82 -> 64); without the bound the
-// compiler takes more registers than these memory-latency-bound kernels can
-// afford.
+// The paired step held to MINB blocks per SM (the launcher's measured
+// choice per lattice and pattern): without the bound the compiler takes more
+// registers than these memory-latency-bound kernels can afford.
 template <class L, int S, int PAT, int MODEL, bool FORCE, int MINB>
 __global__ void __launch_bounds__(kPairThreads, MINB) k_step_pair_bounded(const unsigned short *src,
                                                                           unsigned short *dst,
@@ -562,7 +620,7 @@ __global__ void __launch_bounds__(kPairThreads, MINB) k_step_pair_bounded(const 
 {
     const int y = blockIdx.y, z = blockIdx.z;
     const bool irow = y > 0 && y < p.ny - 1 && (L::D == 2 || (z > 0 && z < p.nz - 1));
-    if (irow)
+    if (irow || PAT == PAT_LOCAL)
         pair_body<L, S, PAT, MODEL, FORCE, true, false>(src, dst, p);
     else
         pair_body<L, S, PAT, MODEL, FORCE, false, false>(src, dst, p);

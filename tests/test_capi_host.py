@@ -155,3 +155,17 @@ def test_noalloc_reduction_refuses_faces_and_obstacles(lib):
     assert lib.lbm_reduce_state_noalloc(lbm.LBM_D3Q19, 8, 8, 8, lbm.LBM_BC_CAVITY,
                                         ctypes.byref(o), ctypes.c_void_p(256), 0, None, None,
                                         out) == lbm.LBM_ERR_ARG
+
+
+def test_noalloc_reduction_refuses_what_lbm_create_refuses(lib):
+    # The same option checks as lbm_create, on the host before any device call.
+    out = (ctypes.c_double * 6)()
+    for field, value in (("compressible", 1), ("rho0", -1.0), ("collision", 7),
+                         ("p_outflow", 0.0)):
+        o = lbm.lbm_default_opts()
+        if field == "compressible":
+            o.storage = lbm.LBM_F16S
+        setattr(o, field, value)
+        assert lib.lbm_reduce_state_noalloc(lbm.LBM_D3Q19, 8, 8, 8, lbm.LBM_BC_CAVITY,
+                                            ctypes.byref(o), ctypes.c_void_p(256), 0, None,
+                                            None, out) == lbm.LBM_ERR_ARG, field

@@ -378,6 +378,33 @@ def test_taylor_green_512(tgv512_ref, storage):
 
 
 # ---------------------------------------------------------------------------
+# FP32 momentum on a periodic box: the collision keeps the total momentum, so
+# a drift measures arithmetic bias.  Every FP32 lattice weight rounds up by
+# 7.45e-9 relative; applied as single floats they scaled the equilibrium's
+# momentum by 1 + 7.45e-9 omega per collision, a drift of ~6e-5 over these
+# 5000 steps (omega = 1.6).  With the weights as hi + lo pairs what is left
+# is unbiased rounding noise.
+
+
+@pytest.mark.parametrize("lattice,shape", [("d2q9", (256, 128, 1)), ("d3q19", (48, 40, 36)),
+                                           ("d3q27", (40, 36, 32))])
+@pytest.mark.parametrize("storage,aa,trt", [("f32", True, None), ("f32", False, None),
+                                            ("f32", True, 3 / 16)])
+def test_fp32_momentum_has_no_drift_on_periodic_box(lattice, shape, storage, aa, trt):
+    from paper_2201_11330_b300.lbm import Lattice
+    Q, d = oracle.dims(lattice)
+    p0, u0 = W.random_smooth_state(*shape, d, amp_u=0.02, seed=61)
+    u0 = u0 + np.array([0.04, -0.03, 0.02][:d]).reshape(d, 1)
+    lat = Lattice(lattice, *shape, 0.625, "periodic", storage=storage, aa=aa, trt_lambda=trt)
+    lat.init(torch.from_numpy(p0).cuda(), torch.from_numpy(np.ascontiguousarray(u0)).cuda())
+    j0 = np.array(lat.reduce()["momentum"][:d])
+    lat.step(5000)
+    j1 = np.array(lat.reduce()["momentum"][:d])
+    drift = np.abs(j1 - j0).max() / np.abs(j0).max()
+    assert drift < 2e-6, drift
+
+
+# ---------------------------------------------------------------------------
 # The paired kernel (16-bit storage, two nodes per thread, shuffle realignment)
 # against the plain kernel: bitwise equal, including row ends, warp and block
 # edges, ragged blocks and 2-node rows.
