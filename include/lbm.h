@@ -132,8 +132,7 @@ typedef enum { LBM_COLL_BGK = 0, LBM_COLL_TRT = 1 } lbm_collision;
 typedef struct {
     int storage;        /* lbm_storage */
     int aa;             /* 0: two-lattice pull scheme; 1: single-lattice AA pattern */
-    int compressible;   /* 0: Eq. (incompressible_feq); 1: Eq. (feq) with rho = sum f
-                           (FP64 / FP32 storage only) */
+    int compressible;   /* 0: Eq. (incompressible_feq); 1: Eq. (feq) with rho = sum f */
     int f32_unshifted;  /* LBM_F32 only: store f itself instead of f - t */
     double rho0;        /* constant density of the incompressible model (> 0) */
     double lid_u[3];    /* moving-wall velocity (ignored for LBM_BC_PERIODIC) */

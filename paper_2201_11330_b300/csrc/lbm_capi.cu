@@ -60,8 +60,6 @@ bool valid_opts(const lbm_opts &o)
     if (o.collision == LBM_COLL_TRT &&
         (o.compressible || !(o.trt_lambda > 0.0 && isfinite(o.trt_lambda))))
         return false;
-    if (o.compressible && (o.storage == LBM_F16S || o.storage == LBM_BF16S))
-        return false;  // the compressible model is built for FP64 / FP32 storage
     if (!(o.rho0 > 0.0) || !isfinite(o.rho0))
         return false;
     if (o.geometry != 0 && o.geometry != 1)

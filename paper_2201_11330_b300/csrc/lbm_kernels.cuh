@@ -243,9 +243,11 @@ __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coe
             pair_eq(A_, sym, asym);
             const R hp = o_mul(sp[a], R(0.5)), hm = o_mul(sm[a], R(0.5));
             const R gp = o_fma(om, o_fma(sym, t, -hp), hp);
+            // odd part: omm (asym t - hm) + hm; in FP32 the weight's lo part is
+            // added to the small difference asym t_hi - hm, where it is not lost
             R gm;
             if constexpr (std::is_same<R, float>::value)
-                gm = o_fma(omm, o_sub(wmul<L, a>(asym), hm), hm);
+                gm = o_fma(omm, o_fma(asym, w_lo<L>(a), o_fma(asym, w_hi<L>(a), -hm)), hm);
             else
                 gm = o_fma(omm, o_fma(asym, t, -hm), hm);
             g[a] = o_add(gp, gm);

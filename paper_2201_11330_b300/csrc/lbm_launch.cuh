@@ -18,9 +18,7 @@ inline cudaError_t with_bool(bool b, F &&f)
 template <int M>
 using model_c = std::integral_constant<int, M>;
 
-// one instantiation per collision model (Model); the compressible model is
-// built for FP64 and FP32 storage only (lbm_create refuses it with 16-bit
-// storage), which keeps the 16-bit translation units' build time down
+// one instantiation per collision model (Model)
 template <int S, class F>
 inline cudaError_t with_model(int m, F &&f)
 {
@@ -28,10 +26,7 @@ inline cudaError_t with_model(int m, F &&f)
     case M_INC:
         return f(model_c<M_INC>{});
     case M_COMP:
-        if constexpr (S == ST_F64 || S == ST_F32)
-            return f(model_c<M_COMP>{});
-        else
-            return cudaErrorInvalidValue;
+        return f(model_c<M_COMP>{});
     case M_TRT:
         return f(model_c<M_TRT>{});
     default:

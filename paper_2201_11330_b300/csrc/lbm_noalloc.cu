@@ -104,11 +104,9 @@ cudaError_t launch_s(const void *state, int form, bool comp, bool force, const S
 {
     using T = typename Sto<S>::T;
     const T *src = (const T *)state;
-    // the compressible model runs with FP64 / FP32 storage only
-    constexpr bool wide = S == ST_F64 || S == ST_F32;
-    return pick(comp && wide, [&](auto C) {
+    return pick(comp, [&](auto C) {
         return pick(force, [&](auto Fo) {
-            constexpr bool c = decltype(C)::value && wide, fo = decltype(Fo)::value;
+            constexpr bool c = decltype(C)::value, fo = decltype(Fo)::value;
             if (form == FORM_LOCAL)
                 k_moments_noalloc<L, S, FORM_LOCAL, c, fo><<<grid, block, 0, st>>>(src, p, partials, xseg);
             else if (form == FORM_SWAPPED)

@@ -212,8 +212,8 @@ __device__ __forceinline__ void collide2w(unsigned (&W)[L::Q], bool top, const f
             const float2 hp = v_mul(v_add(ga, gb), v_bc(0.5f));
             const float2 hm = v_mul(v_sub(ga, gb), v_bc(0.5f));
             const float2 gp = v_fma(om, v_fma(sym, t, v_neg(hp)), hp);
-            const float2 at = v_fma(asym, t, v_mul(asym, v_bc(w_lo<L>(a))));
-            const float2 gm = v_fma(omm, v_sub(at, hm), hm);
+            const float2 gm =
+                v_fma(omm, v_fma(asym, v_bc(w_lo<L>(a)), v_fma(asym, t, v_neg(hm))), hm);
             W[a] = enc2<S>(v_add(gp, gm));
             W[b] = enc2<S>(v_sub(gp, gm));
         });

@@ -97,11 +97,11 @@ def test_create_validates_before_touching_memory(lib):
     o.trt_lambda = 3 / 16
     o.compressible = 1
     assert _create(lib, opts=o)[0] == lbm.LBM_ERR_ARG
-    # the compressible model runs with FP64 / FP32 storage
+    # the compressible model runs with every storage type
     o = lbm.lbm_default_opts()
     o.compressible = 1
     for st, rc in ((lbm.LBM_F64, lbm.LBM_OK), (lbm.LBM_F32, lbm.LBM_OK),
-                   (lbm.LBM_F16S, lbm.LBM_ERR_ARG), (lbm.LBM_BF16S, lbm.LBM_ERR_ARG)):
+                   (lbm.LBM_F16S, lbm.LBM_OK), (lbm.LBM_BF16S, lbm.LBM_OK)):
         o.storage = st
         r, ctx = _create(lib, opts=o)
         assert r == rc, st
@@ -160,11 +160,11 @@ def test_noalloc_reduction_refuses_faces_and_obstacles(lib):
 def test_noalloc_reduction_refuses_what_lbm_create_refuses(lib):
     # The same option checks as lbm_create, on the host before any device call.
     out = (ctypes.c_double * 6)()
-    for field, value in (("compressible", 1), ("rho0", -1.0), ("collision", 7),
-                         ("p_outflow", 0.0)):
+    for field, value in (("storage", 9), ("rho0", -1.0), ("collision", 7),
+                         ("p_outflow", 0.0), ("trt_lambda", -1.0)):
         o = lbm.lbm_default_opts()
-        if field == "compressible":
-            o.storage = lbm.LBM_F16S
+        if field == "trt_lambda":
+            o.collision = lbm.LBM_COLL_TRT
         setattr(o, field, value)
         assert lib.lbm_reduce_state_noalloc(lbm.LBM_D3Q19, 8, 8, 8, lbm.LBM_BC_CAVITY,
                                             ctypes.byref(o), ctypes.c_void_p(256), 0, None,

@@ -123,7 +123,7 @@ def test_random_state_parity(lattice, shape, bc, storage, aa):
 @pytest.mark.parametrize("lattice,shape,bc", [("d3q19", (21, 18, 14), "cavity"),
                                               ("d2q9", (40, 31, 1), "periodic"),
                                               ("d3q27", (15, 13, 12), "channel")])
-@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s"])
 def test_compressible_parity(lattice, shape, bc, storage):
     Q, d = oracle.dims(lattice)
     nx, ny, nz = shape
@@ -439,6 +439,21 @@ def test_paired_equals_plain_bitwise(lattice, shape, storage, bc):
         a = _variant_run(lattice, shape, bc, storage, aa, steps, "plain", force)
         b = _variant_run(lattice, shape, bc, storage, aa, steps, "paired", force)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), (aa, steps, force)
+
+
+@pytest.mark.parametrize("lattice,shape", [("d3q19", (66, 13, 11)), ("d3q27", (264, 7, 6)),
+                                           ("d2q9", (300, 37, 1))])
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+def test_compressible_paired_equals_plain_bitwise(lattice, shape, storage):
+    Q, d = oracle.dims(lattice)
+    p0, u0 = W.random_smooth_state(*shape, d, amp_u=0.04, amp_p=5e-3, seed=46)
+    F = W.fourier_force(*shape, amplitude=2e-5, seed=10, dims=d)
+    for aa, steps in ((False, 9), (True, 9), (True, 10)):
+        outs = [gpu_run(lattice, shape, 0.6, "cavity", steps, storage=storage, aa=aa,
+                        lid=(0.07, 0.0, 0.01), p0=p0, u0=u0, F=F, compressible=True, kernel=k)
+                for k in ("plain", "paired")]
+        assert outs[0][2].kernel == "plain" and outs[1][2].kernel == "paired"
+        assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
 
 
 # ---------------------------------------------------------------------------
