@@ -218,13 +218,18 @@ def run_cavity(lattice, n, re, storage, aa, steps, warmup, world, device, trt_la
     bytes_per_node = 2 * Q_OF[lattice] * BYTES_OF[storage]
     out = {"glups": glups, "ms_per_step": total / steps, "bytes_per_node": bytes_per_node,
            "nodes": N}
+    tag = f"{lattice}_{storage}{'_trt' if trt_lambda else ''}"
     if aa:
         g = [d for d, p in zip(durs, parity) if p == 0]
         l = [d for d, p in zip(durs, parity) if p == 1]
         out["gather_ms"] = statistics.mean(g) if g else None
         out["local_ms"] = statistics.mean(l) if l else None
+        out["traffic_gather"] = load_traffic(f"{tag}_gather_{n}")
+        out["traffic_local"] = load_traffic(f"{tag}_local_{n}")
     else:
         out["pull_ms"] = statistics.mean(durs)
+        out["traffic_pull"] = load_traffic(f"{tag}_pull_{n}")
+    out["algorithmic_bytes_per_launch"] = N * bytes_per_node
     r = lat.reduce()
     out["mass_rel_drift"] = abs(r["mass"] - N) / N
     out["max_speed"] = r["max_speed"]
@@ -504,6 +509,11 @@ def main():
                     help="lattice of the headline run (profiling of the D3Q27 kernels)")
     ap.add_argument("--pull", action="store_true",
                     help="two-lattice pull scheme for the headline run (profiling)")
+    ap.add_argument("--trt", action="store_true",
+                    help="two-relaxation-time collision (Lambda = 3/16) for the headline run "
+                         "(profiling)")
+    ap.add_argument("--e2e", action="store_true",
+                    help="with --no-extras: still run the two end-to-end legs (profiling)")
     ap.add_argument("--workload", default="cavity", choices=["cavity", "sphere"],
                     help="sphere: only the paper's D3Q27 sphere flow at --storage (profiling)")
     ap.add_argument("--no-extras", action="store_true",
@@ -549,7 +559,7 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     head = run_cavity(hb["lattice"], hb["n"], hb["re"], hb["storage"], hb["aa"], args.steps,
-                      args.warmup, world, device)
+                      args.warmup, world, device, trt_lambda=3 / 16 if args.trt else None)
     clocks = sampler.stop()
 
     N = head["nodes"]
@@ -565,7 +575,8 @@ def main():
         pat = "PULL"
     dom_name = f"k_step<{lat_tag},{st_tag},{pat}>"
     achieved = N * bpn / (dom_ms * 1e-3) / 1e9
-    traffic = load_traffic(f"{hb['lattice']}_{hb['storage']}_{pat.lower()}_{hb['n']}")
+    traffic = load_traffic(f"{hb['lattice']}_{hb['storage']}{'_trt' if args.trt else ''}_"
+                           f"{pat.lower()}_{hb['n']}")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": dom_name, "peak_kind": f"{peak_kind} copy bandwidth",
@@ -608,7 +619,7 @@ def main():
     # and the stepping call with one monitor read at the end; at least 100
     # steps so that the one-off host copies do not swamp the steps
     e2e = e2e_step_n = None
-    if not args.no_extras:
+    if not args.no_extras or args.e2e:
         e2e_steps = max(100, args.steps)
         e2e = run_e2e(hb["n"], hb["re"], hb["storage"], e2e_steps, args.warmup, world, device)
         e2e_step_n = run_e2e(hb["n"], hb["re"], hb["storage"], e2e_steps, args.warmup, world,

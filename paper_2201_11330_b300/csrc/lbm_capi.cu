@@ -437,8 +437,25 @@ int ctx_launch_moments(lbm_ctx *c, const void *src, int form, void *p_out, void 
     l.mp.xseg = (c->nx + c->bx - 1) / c->bx;
     l.mp.nseg = l.mp.xseg * c->ny * c->nz;
     l.mp.links = c->sp.links;
+    // persistent blocks, grid-stride over the row segments (measured faster
+    // than one segment per block with a chunked reduction of the partials)
     l.grid = dim3(c->nred, 1, 1);
     return dispatch(c->lattice, l) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+int ctx_reduce_state(lbm_ctx *c, const void *src, int form, double r[6])
+{
+    int rc = ctx_launch_moments(c, src, form, nullptr, nullptr, 0, c->partials);
+    if (rc != LBM_OK)
+        return rc;
+    if (launch_finish(c->partials, c->nred, c->result, c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    if (cudaMemcpyAsync(r, c->result, kReduceVals * sizeof(double), cudaMemcpyDeviceToHost,
+                        c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    return LBM_OK;
 }
 
 int ctx_current_form(const lbm_ctx *c)
@@ -909,18 +926,10 @@ int lbm_reduce(lbm_ctx *c, double *out)
         return LBM_ERR_ARG;
     if (!c->initialized)
         return LBM_ERR_STATE;
-    int rc = ctx_launch_moments(c, ctx_state(c), ctx_current_form(c), nullptr, nullptr, 0,
-                                c->partials);
+    double r[kReduceVals];
+    const int rc = ctx_reduce_state(c, ctx_state(c), ctx_current_form(c), r);
     if (rc != LBM_OK)
         return rc;
-    if (launch_finish(c->partials, c->nred, c->result, c->stream) != cudaSuccess)
-        return LBM_ERR_CUDA;
-    double r[kReduceVals];
-    if (cudaMemcpyAsync(r, c->result, sizeof(r), cudaMemcpyDeviceToHost, c->stream) !=
-        cudaSuccess)
-        return LBM_ERR_CUDA;
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess)
-        return LBM_ERR_CUDA;
     out[0] = r[0] + (c->shifted ? (double)c->n_fluid : 0.0);
     out[1] = r[1];
     out[2] = r[2];

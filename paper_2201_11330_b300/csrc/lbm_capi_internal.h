@@ -68,6 +68,9 @@ int ctx_launch_step(lbm_ctx *c, const void *src, void *dst, int pattern, void *u
                     long long *reduce_blocks = nullptr, bool obstacle_force = false);
 int ctx_launch_moments(lbm_ctx *c, const void *src, int form, void *p_out, void *u_out,
                        int out_f32, double *partials);
+// the six monitor sums of a state (per-block FP64 partials of the moments
+// kernel, then a fixed-order reduction); synchronises the stream
+int ctx_reduce_state(lbm_ctx *c, const void *src, int form, double r[6]);
 int ctx_current_form(const lbm_ctx *c);
 const void *ctx_state(const lbm_ctx *c);
 }  // namespace lbm

@@ -773,10 +773,44 @@ __device__ __forceinline__ R warp_max(R v)
     return v;
 }
 
-// Node n's moments from a stored state in form FORM: s = sum of the stored
-// populations (the shifted pressure sum), rho, and u = (j* - F/2)/rho from
-// the post-collision momentum j* = j + F.  Shared by every kernel that
-// reduces or outputs the moments of a state, so that they agree bit for bit.
+// Moments of one node from its populations g (in the storage's shift): s =
+// sum g (the shifted pressure sum), rho, and u = (j* - F/2)/rho from the
+// post-collision momentum j* = j + F.  Shared by every kernel that reduces or
+// outputs the moments of a state, so that they agree bit for bit.
+template <class L, class R, bool COMP, bool FORCE>
+__device__ __forceinline__ void moments_of(const R (&g)[L::Q], const StepParams &p, int n, R &s,
+                                           R &rho, R (&u)[3])
+{
+    constexpr int Q = L::Q;
+    const Coef<R> &c = coef<R>(p);
+    const size_t N = (size_t)p.N;
+    R j[3] = {R(0), R(0), R(0)};
+    s = R(0);
+    SFor<0, Q>::run([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        s = o_add(s, g[a]);
+        SFor<0, 3>::run([&](auto K_) {
+            constexpr int k = decltype(K_)::value;
+            if constexpr (L::e(a, k) == 1)
+                j[k] = o_add(j[k], g[a]);
+            else if constexpr (L::e(a, k) == -1)
+                j[k] = o_sub(j[k], g[a]);
+        });
+    });
+    rho = COMP ? o_add(s, c.sigma) : c.rho0;
+    const R ir = COMP ? R(1) / rho : c.inv_rho0;
+    for (int k = 0; k < 3; ++k) {
+        R jk = j[k];
+        if constexpr (FORCE) {
+            if (k < L::D)
+                jk = o_fma(R(-0.5), R(p.F[k * N + n]), jk);
+        }
+        u[k] = o_mul(jk, ir);
+    }
+}
+
+// Node n's moments from a stored state in form FORM (moments_of on the
+// populations entering the node).
 template <class L, int S, int FORM, bool COMP, bool FORCE>
 __device__ __forceinline__ void node_moments(const typename Sto<S>::T *src, const StepParams &p,
                                              int x, int y, int z, int n,
@@ -785,7 +819,6 @@ __device__ __forceinline__ void node_moments(const typename Sto<S>::T *src, cons
 {
     using R = typename Sto<S>::R;
     constexpr int Q = L::Q;
-    const Coef<R> &c = coef<R>(p);
     const size_t N = (size_t)p.N;
     R g[Q];
     if constexpr (FORM == FORM_LOCAL) {
@@ -814,29 +847,7 @@ __device__ __forceinline__ void node_moments(const typename Sto<S>::T *src, cons
             }
         });
     }
-    R j[3] = {R(0), R(0), R(0)};
-    s = R(0);
-    SFor<0, Q>::run([&](auto A_) {
-        constexpr int a = decltype(A_)::value;
-        s = o_add(s, g[a]);
-        SFor<0, 3>::run([&](auto K_) {
-            constexpr int k = decltype(K_)::value;
-            if constexpr (L::e(a, k) == 1)
-                j[k] = o_add(j[k], g[a]);
-            else if constexpr (L::e(a, k) == -1)
-                j[k] = o_sub(j[k], g[a]);
-        });
-    });
-    rho = COMP ? o_add(s, c.sigma) : c.rho0;
-    const R ir = COMP ? R(1) / rho : c.inv_rho0;
-    for (int k = 0; k < 3; ++k) {
-        R jk = j[k];
-        if constexpr (FORCE) {
-            if (k < L::D)
-                jk = o_fma(R(-0.5), R(p.F[k * N + n]), jk);
-        }
-        u[k] = o_mul(jk, ir);
-    }
+    moments_of<L, R, COMP, FORCE>(g, p, n, s, rho, u);
 }
 
 // Grid-stride over x-segments of rows; each block keeps FP64 partial sums of
@@ -849,7 +860,12 @@ __global__ void __launch_bounds__(256) k_moments(const typename Sto<S>::T *src, 
     using R = typename Sto<S>::R;
     const Coef<R> &c = coef<R>(p);
     const size_t N = (size_t)p.N;
-    double acc[kReduceVals] = {0, 0, 0, 0, 0, 0};
+    // lane k < 5 keeps the FP64 running sum of monitor value k: one FP64 add
+    // per warp and segment instead of five (B300's FP64 rate is a small
+    // fraction of FP32); the maximum stays in the kernel's arithmetic, where
+    // it is exact
+    double acc = 0.0;
+    R accmax = R(0);
     const int lane = threadIdx.x & 31;
     for (int seg = blockIdx.x; seg < m.nseg; seg += gridDim.x) {
         const int xs = seg % m.xseg;
@@ -897,24 +913,25 @@ __global__ void __launch_bounds__(256) k_moments(const typename Sto<S>::T *src, 
             monitor_values(s_, rho, u, vals);
         }
         if (m.partials) {
+            R mine = R(0);
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
                 const R w = warp_sum(vals[k]);
-                if (lane == 0)
-                    acc[k] += double(w);
+                mine = lane == k ? w : mine;
             }
-            const R mx = warp_max(vals[5]);
-            if (lane == 0)
-                acc[5] = fmax(acc[5], double(mx));
+            if (lane < 5)
+                acc += double(mine);
+            accmax = max(accmax, warp_max(vals[5]));
         }
     }
     if (!m.partials)
         return;
     __shared__ double sh[8][kReduceVals];
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    if (lane == 0)
-        for (int k = 0; k < kReduceVals; ++k)
-            sh[warp][k] = acc[k];
+    if (lane < 5)
+        sh[warp][lane] = acc;
+    else if (lane == 5)
+        sh[warp][5] = double(accmax);
     __syncthreads();
     if (threadIdx.x < kReduceVals) {
         const int k = threadIdx.x;

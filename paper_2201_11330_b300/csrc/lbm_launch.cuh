@@ -246,6 +246,23 @@ cudaError_t launch_storage(const Launch &l)
         return with_bool(l.comp, [&](auto C) {
             return with_bool(l.force, [&](auto Fo) {
                 constexpr bool c = decltype(C)::value, fo = decltype(Fo)::value;
+                if constexpr (S == ST_F16S || S == ST_BF16S) {
+                    // 16-bit storage, the node's own slots: two nodes per
+                    // thread, one 32-bit load per slot
+                    if (l.pattern != FORM_STREAMED && l.sp.nx % 2 == 0) {
+                        MomParams mp = l.mp;
+                        mp.xseg = (l.sp.nx + 2 * kPairThreads - 1) / (2 * kPairThreads);
+                        mp.nseg = mp.xseg * l.sp.ny * l.sp.nz;
+                        const auto *s16 = (const unsigned short *)l.src;
+                        if (l.pattern == FORM_LOCAL)
+                            k_moments_pair<L, S, FORM_LOCAL, c, fo>
+                                <<<l.grid, kPairThreads, 0, l.stream>>>(s16, l.sp, mp);
+                        else
+                            k_moments_pair<L, S, FORM_SWAPPED, c, fo>
+                                <<<l.grid, kPairThreads, 0, l.stream>>>(s16, l.sp, mp);
+                        return cudaGetLastError();
+                    }
+                }
                 switch (l.pattern) {
                 case FORM_LOCAL:
                     k_moments<L, S, FORM_LOCAL, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, l.sp, l.mp);

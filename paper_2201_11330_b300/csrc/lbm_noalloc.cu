@@ -57,7 +57,10 @@ __global__ void __launch_bounds__(256) k_moments_noalloc(const typename Sto<S>::
     const int xs = blockIdx.x, z = blockIdx.y, c0 = blockIdx.z;
     const int x = xs * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    double acc[kReduceVals] = {0, 0, 0, 0, 0, 0};
+    // lane k < 5 keeps the FP64 running sum of value k (one FP64 add per warp
+    // and row, as k_moments); the maximum stays in the kernel's arithmetic
+    double acc = 0.0;
+    R accmax = R(0);
     for (int y = c0; y < p.ny; y += gridDim.z) {
         R vals[kReduceVals] = {R(0), R(0), R(0), R(0), R(0), R(0)};
         if (x < p.nx) {
@@ -66,21 +69,22 @@ __global__ void __launch_bounds__(256) k_moments_noalloc(const typename Sto<S>::
             node_moments<L, S, FORM, COMP, FORCE>(src, p, x, y, z, n, s, rho, u);
             monitor_values(s, rho, u, vals);
         }
+        R mine = R(0);
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             const R w = warp_sum(vals[k]);
-            if (lane == 0)
-                acc[k] += double(w);
+            mine = lane == k ? w : mine;
         }
-        const R mx = warp_max(vals[5]);
-        if (lane == 0)
-            acc[5] = fmax(acc[5], double(mx));
+        if (lane < 5)
+            acc += double(mine);
+        accmax = max(accmax, warp_max(vals[5]));
     }
     __shared__ double sh[8][kReduceVals];
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    if (lane == 0)
-        for (int k = 0; k < kReduceVals; ++k)
-            sh[warp][k] = acc[k];
+    if (lane < 5)
+        sh[warp][lane] = acc;
+    else if (lane == 5)
+        sh[warp][5] = double(accmax);
     __syncthreads();
     if (threadIdx.x < kReduceVals) {
         const int k = threadIdx.x;

@@ -589,6 +589,140 @@ __device__ __forceinline__ void pair_body(const unsigned short *src, unsigned sh
         block_monitor(mon, p.partials, grid_block_index());
 }
 
+// ---- moments + FP64 reduction, 16-bit storage, two nodes per thread ------------
+// k_moments for the LOCAL and SWAPPED forms (each node's own slots) with one
+// 32-bit load per slot for two adjacent nodes.  Per node the values are those
+// of k_moments (moments_of, monitor_values), and so is every FP32 sum over a
+// group of 32 consecutive nodes of a row segment: the one-node kernel's warp
+// butterfly (xor 16, 8, 4, 2, 1 over the node index) is node 2t+h of the
+// group = half h of lane t, i.e. xor 8, 4, 2, 1 over the lanes of each half
+// warp and, last, the thread's two halves.  Only the FP64 accumulation of the
+// group sums runs in another order.  Grid-stride over segments of 256 nodes;
+// block b writes partials[b].  nx even.
+template <class L, int S, int FORM, bool COMP, bool FORCE>
+__global__ void __launch_bounds__(kPairThreads) k_moments_pair(const unsigned short *src,
+                                                              const StepParams p,
+                                                              const MomParams m)
+{
+    static_assert(FORM == FORM_LOCAL || FORM == FORM_SWAPPED, "the node's own slots only");
+    using R = float;
+    constexpr int Q = L::Q;
+    const Coef<R> &c = p.cf;
+    const size_t N = (size_t)p.N;
+    const int lane = threadIdx.x & 31;
+    // lane k < 5 of each half warp keeps the FP64 running sum of monitor value
+    // k of its 32-node group (one FP64 add per warp and segment); the maximum
+    // stays in FP32, where it is exact
+    double acc = 0.0;
+    R accmax = R(0);
+    const int hk = lane & 15;
+    for (int seg = blockIdx.x; seg < m.nseg; seg += gridDim.x) {
+        const int xs = seg % m.xseg;
+        const int row = seg / m.xseg;
+        const int y = row % p.ny, z = row / p.ny;
+        const int x = xs * (2 * kPairThreads) + 2 * threadIdx.x;
+        const bool active = x < p.nx;
+        const int n0 = x + p.nx * (y + p.ny * z);
+        unsigned W[Q];
+        SFor<0, Q>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            constexpr int slot = FORM == FORM_LOCAL ? a : opp<L>(a);
+            W[a] = active ? *reinterpret_cast<const unsigned *>(src + (size_t)slot * N + n0) : 0u;
+        });
+        R vals[2][kReduceVals];
+        for (int h = 0; h < 2; ++h) {
+            for (int k = 0; k < kReduceVals; ++k)
+                vals[h][k] = R(0);
+            const int n = n0 + h;
+            const bool solid = active && m.links && (m.links[n] >> 31);
+            if (solid) {
+                if (m.p_out) {
+                    if (m.out_f32)
+                        ((float *)m.p_out)[n] = 0.f;
+                    else
+                        ((double *)m.p_out)[n] = 0.0;
+                }
+                if (m.u_out) {
+                    for (int k = 0; k < L::D; ++k) {
+                        if (m.out_f32)
+                            ((float *)m.u_out)[k * N + n] = 0.f;
+                        else
+                            ((double *)m.u_out)[k * N + n] = 0.0;
+                    }
+                }
+            }
+            if (active && !solid) {
+                R g[Q];
+                SFor<0, Q>::run([&](auto A_) {
+                    constexpr int a = decltype(A_)::value;
+                    const float2 v = dec2<S>(W[a]);
+                    g[a] = h ? v.y : v.x;
+                });
+                R s_, rho, u[3];
+                moments_of<L, R, COMP, FORCE>(g, p, n, s_, rho, u);
+                if (m.p_out) {
+                    const R pv = (s_ + c.sigma) * R(1.0 / 3.0);
+                    if (m.out_f32)
+                        ((float *)m.p_out)[n] = float(pv);
+                    else
+                        ((double *)m.p_out)[n] = double(pv);
+                }
+                if (m.u_out) {
+                    for (int k = 0; k < L::D; ++k) {
+                        if (m.out_f32)
+                            ((float *)m.u_out)[k * N + n] = float(u[k]);
+                        else
+                            ((double *)m.u_out)[k * N + n] = double(u[k]);
+                    }
+                }
+                monitor_values(s_, rho, u, vals[h]);
+            }
+        }
+        if (m.partials) {
+            R mine = R(0);
+#pragma unroll
+            for (int k = 0; k < kReduceVals; ++k) {
+                R v0 = vals[0][k], v1 = vals[1][k];
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) {
+                    const R w0 = __shfl_xor_sync(0xffffffffu, v0, o);
+                    const R w1 = __shfl_xor_sync(0xffffffffu, v1, o);
+                    if (k == 5) {
+                        v0 = max(v0, w0);
+                        v1 = max(v1, w1);
+                    } else {
+                        v0 += w0;
+                        v1 += w1;
+                    }
+                }
+                // the 32-node group's value
+                if (k == 5)
+                    accmax = max(accmax, max(v0, v1));
+                else
+                    mine = hk == k ? v0 + v1 : mine;
+            }
+            if (hk < 5)
+                acc += double(mine);
+        }
+    }
+    if (!m.partials)
+        return;
+    __shared__ double sh[2 * kPairThreads / 32][kReduceVals];
+    const int grp = threadIdx.x >> 4;  // 32-node group of the block
+    if (hk < 5)
+        sh[grp][hk] = acc;
+    else if (hk == 5)
+        sh[grp][5] = double(accmax);
+    __syncthreads();
+    if (threadIdx.x < kReduceVals) {
+        const int k = threadIdx.x;
+        double r = sh[0][k];
+        for (int i = 1; i < 2 * kPairThreads / 32; ++i)
+            r = (k == 5) ? fmax(r, sh[i][k]) : r + sh[i][k];
+        m.partials[blockIdx.x * kPartialStride + k] = r;
+    }
+}
+
 // The pull step of a box with per-face boundaries or obstacles on the pairs
 // the paired kernel can update (see k_step_skip).  MON: 0, 1 = monitor sums,
 // 2 = obstacle force (zero here).  Six blocks per SM, as the bounded D3Q27
