@@ -151,7 +151,7 @@ __device__ __forceinline__ void adjoint_node(const StepParams &p, const AdjParam
 // grid as k_step.  Blocks on the top row (y = ny-1) also add their lid
 // contribution to gU_part[(z * xseg + blockIdx.x) * 4 + k].
 template <class L, class R, bool FORCE>
-__global__ void __launch_bounds__(256) k_adjoint(const StepParams p, const AdjParams ap)
+__device__ __forceinline__ void adjoint_kernel_body(const StepParams &p, const AdjParams &ap)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
@@ -179,6 +179,21 @@ __global__ void __launch_bounds__(256) k_adjoint(const StepParams p, const AdjPa
             r += sh[w][threadIdx.x];
         ap.gU_part[((size_t)z * ap.xseg + blockIdx.x) * 4 + threadIdx.x] += r;
     }
+}
+
+template <class L, class R, bool FORCE>
+__global__ void __launch_bounds__(256) k_adjoint(const StepParams p, const AdjParams ap)
+{
+    adjoint_kernel_body<L, R, FORCE>(p, ap);
+}
+
+// The FP32 adjoint step with a force held to MINB blocks per SM: unbounded it
+// takes 63-64 registers (four blocks per SM) and is memory-latency bound.
+template <class L, class R, bool FORCE, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_adjoint_bounded(const StepParams p,
+                                                               const AdjParams ap)
+{
+    adjoint_kernel_body<L, R, FORCE>(p, ap);
 }
 
 // Seed at T: lambda_a = e_a . u^T, gF = u^T / 2 (the direct dJ/dF term).

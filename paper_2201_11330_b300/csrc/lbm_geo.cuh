@@ -293,8 +293,8 @@ __device__ __forceinline__ void geo_node(const typename Sto<S>::T *src, typename
 // per-block monitor sums, 2 = per-block obstacle force sums, both into
 // p.partials.
 template <class L, int S, int MODEL, bool FORCE, int MON>
-__global__ void __launch_bounds__(256) k_step_geo(const typename Sto<S>::T *src,
-                                                  typename Sto<S>::T *dst, const StepParams p)
+__device__ __forceinline__ void geo_kernel_body(const typename Sto<S>::T *src,
+                                                typename Sto<S>::T *dst, const StepParams &p)
 {
     using R = typename Sto<S>::R;
     R mon[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
@@ -336,6 +336,24 @@ __global__ void __launch_bounds__(256) k_step_geo(const typename Sto<S>::T *src,
         R v[6] = {fo[0], fo[1], fo[2], R(0), R(0), R(0)};
         block_monitor(v, p.partials, bid);
     }
+}
+
+template <class L, int S, int MODEL, bool FORCE, int MON>
+__global__ void __launch_bounds__(256) k_step_geo(const typename Sto<S>::T *src,
+                                                  typename Sto<S>::T *dst, const StepParams p)
+{
+    geo_kernel_body<L, S, MODEL, FORCE, MON>(src, dst, p);
+}
+
+// The general kernel held to three blocks per SM (FP32 and 16-bit storage;
+// unbounded the D3Q27 form takes 88-90 registers, two blocks per SM, and its
+// node-list launch is memory-latency bound).
+template <class L, int S, int MODEL, bool FORCE, int MON>
+__global__ void __launch_bounds__(256, 3) k_step_geo_bounded(const typename Sto<S>::T *src,
+                                                              typename Sto<S>::T *dst,
+                                                              const StepParams p)
+{
+    geo_kernel_body<L, S, MODEL, FORCE, MON>(src, dst, p);
 }
 
 // flags[n] = 1 for the nodes the plain kernel cannot update (needs_general);

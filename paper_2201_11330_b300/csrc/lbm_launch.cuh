@@ -96,12 +96,21 @@ cudaError_t launch_storage(const Launch &l)
             return with_bool(l.force, [&](auto Fo) {
                 constexpr int c = decltype(C)::value;
                 constexpr bool fo = decltype(Fo)::value;
+                auto go = [&](auto Mo) {
+                    constexpr int mo = decltype(Mo)::value;
+                    if constexpr (S == ST_F64)  // FP64-ALU bound: unbounded
+                        k_step_geo<L, S, c, fo, mo><<<l.grid, l.block, 0, l.stream>>>(src, dst,
+                                                                                    l.sp);
+                    else
+                        k_step_geo_bounded<L, S, c, fo, mo>
+                            <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                };
                 if (l.mon == 1)
-                    k_step_geo<L, S, c, fo, 1><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                    go(std::integral_constant<int, 1>{});
                 else if (l.mon == 2)
-                    k_step_geo<L, S, c, fo, 2><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                    go(std::integral_constant<int, 2>{});
                 else
-                    k_step_geo<L, S, c, fo, 0><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                    go(std::integral_constant<int, 0>{});
                 return cudaGetLastError();
             });
         });
@@ -227,7 +236,11 @@ cudaError_t launch_storage(const Launch &l)
     if (l.kind == K_ADJ) {
         using R = typename Sto<S>::R;
         return with_bool(l.force, [&](auto Fo) {
-            k_adjoint<L, R, decltype(Fo)::value><<<l.grid, l.block, 0, l.stream>>>(l.sp, l.ap);
+            constexpr bool fo = decltype(Fo)::value;
+            if constexpr (std::is_same<R, float>::value && fo && L::Q == 19)
+                k_adjoint_bounded<L, R, fo, 5><<<l.grid, l.block, 0, l.stream>>>(l.sp, l.ap);
+            else
+                k_adjoint<L, R, fo><<<l.grid, l.block, 0, l.stream>>>(l.sp, l.ap);
             return cudaGetLastError();
         });
     }
