@@ -52,11 +52,11 @@ def _load():
         lib.or_equilibrium.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, dp, dp]
         lib.or_collide_node.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                                        ctypes.c_double, dp, dp, dp, ctypes.c_double]
+                                        ctypes.c_double, dp, dp, dp, ctypes.c_double, dp]
         lib.or_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                dp, dp, dp, dp, ctypes.c_long, dp, dp, dp, ctypes.c_int,
-                               ctypes.c_double]
+                               ctypes.c_double, dp]
         lib.or_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_double, ctypes.c_int, ctypes.c_double, dp, dp, dp,
                                    dp, ctypes.c_long, ctypes.c_long, dp, dp, dp, ctypes.c_int]
@@ -64,7 +64,7 @@ def _load():
         lib.or_run_faces.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_double, ip, ctypes.c_int, ctypes.c_double,
                                      dp, dp, up, dp, dp, dp, ctypes.c_double, ctypes.c_long,
-                                     dp, dp, dp, dp, ctypes.c_int, ctypes.c_double]
+                                     dp, dp, dp, dp, ctypes.c_int, ctypes.c_double, dp]
         for f in (lib.or_tables, lib.or_equilibrium, lib.or_collide_node, lib.or_run,
                   lib.or_adjoint, lib.or_run_faces):
             f.restype = ctypes.c_int
@@ -130,11 +130,20 @@ def equilibrium(lattice, P, u, rho0=1.0, compressible=False):
     return out
 
 
-def collide_node(lattice, f, tau, rho0=1.0, compressible=False, F=None, trt_lambda=None):
+def _mrt3(mrt):
+    """(s_bulk, s_even, s_odd) of the multiple-relaxation-time collision, or None."""
+    if mrt is None:
+        return None
+    return _f64(np.asarray(mrt, float), 3)
+
+
+def collide_node(lattice, f, tau, rho0=1.0, compressible=False, F=None, trt_lambda=None,
+                 mrt=None):
     """Eq. (collision) at one node (with the Guo source when F is given).
 
     ``trt_lambda`` selects the two-relaxation-time collision with that magic
-    parameter instead of BGK."""
+    parameter instead of BGK; ``mrt = (s_bulk, s_even, s_odd)`` the
+    multiple-relaxation-time collision (stress moments at 1/tau)."""
     lib = _load()
     Q, _ = dims(lattice)
     f = _f64(f, Q)
@@ -144,7 +153,8 @@ def collide_node(lattice, f, tau, rho0=1.0, compressible=False, F=None, trt_lamb
         F3 = np.zeros(3)
         F3[: len(F)] = F
     rc = lib.or_collide_node(_lat(lattice), float(tau), int(bool(compressible)), float(rho0),
-                             _dp(f), _dp(F3), _dp(out), float(trt_lambda or 0.0))
+                             _dp(f), _dp(F3), _dp(out), float(trt_lambda or 0.0),
+                             _dp(_mrt3(mrt)))
     assert rc == 0
     return out
 
@@ -159,12 +169,13 @@ def faces_of(bc):
 
 def run(lattice, nx, ny, nz, tau, bc, steps, *, rho0=1.0, compressible=False, lid=None,
         F=None, p0=None, u0=None, want_f=False, threads=0, trt_lambda=None, solid=None,
-        inlet=None, want_force=False, p_outflow=1.0 / 3.0):
+        inlet=None, want_force=False, p_outflow=1.0 / 3.0, mrt=None):
     """Forward run of Sec. 3.1's loop for ``steps`` steps.
 
     Returns ``(p, u)`` (or ``(p, u, f)``): p shape (N,), u shape (d, N),
     f shape (Q, N) post-propagation.  ``threads=0`` leaves OpenMP's default.
-    ``trt_lambda`` selects the two-relaxation-time collision.
+    ``trt_lambda`` selects the two-relaxation-time collision, ``mrt = (s_bulk,
+    s_even, s_odd)`` the multiple-relaxation-time collision.
 
     ``bc`` is "periodic", "cavity", "channel" or a sequence of six face
     types ("periodic", "wall", "inlet", "outflow", "symmetry", "nodal"; order -x, +x,
@@ -179,7 +190,7 @@ def run(lattice, nx, ny, nz, tau, bc, steps, *, rho0=1.0, compressible=False, li
         return _run_faces(lattice, nx, ny, nz, tau, bc, steps, rho0=rho0,
                           compressible=compressible, lid=lid, F=F, p0=p0, u0=u0, want_f=want_f,
                           threads=threads, trt_lambda=trt_lambda, solid=solid, inlet=inlet,
-                          want_force=want_force, p_outflow=p_outflow)
+                          want_force=want_force, p_outflow=p_outflow, mrt=mrt)
     lib = _load()
     Q, d = dims(lattice)
     N = nx * ny * nz
@@ -192,7 +203,7 @@ def run(lattice, nx, ny, nz, tau, bc, steps, *, rho0=1.0, compressible=False, li
     f = np.zeros(Q * N) if want_f else None
     rc = lib.or_run(_lat(lattice), nx, ny, nz, float(tau), _bc(bc), int(bool(compressible)),
                     float(rho0), _dp(lid3), _dp(F), _dp(p0), _dp(u0), int(steps), _dp(p),
-                    _dp(u), _dp(f), int(threads), float(trt_lambda or 0.0))
+                    _dp(u), _dp(f), int(threads), float(trt_lambda or 0.0), _dp(_mrt3(mrt)))
     if rc != 0:
         raise ValueError(f"or_run failed with status {rc}")
     u = u.reshape(d, N)
@@ -202,7 +213,7 @@ def run(lattice, nx, ny, nz, tau, bc, steps, *, rho0=1.0, compressible=False, li
 
 
 def _run_faces(lattice, nx, ny, nz, tau, bc, steps, *, rho0, compressible, lid, F, p0, u0,
-               want_f, threads, trt_lambda, solid, inlet, want_force, p_outflow):
+               want_f, threads, trt_lambda, solid, inlet, want_force, p_outflow, mrt=None):
     lib = _load()
     Q, d = dims(lattice)
     N = nx * ny * nz
@@ -231,7 +242,7 @@ def _run_faces(lattice, nx, ny, nz, tau, bc, steps, *, rho0, compressible, lid, 
                               ctypes.POINTER(ctypes.c_ubyte)),
                           _dp(inl), _dp(p0), _dp(u0), float(p_outflow), int(steps), _dp(p),
                           _dp(u), _dp(f),
-                          _dp(force), int(threads), float(trt_lambda or 0.0))
+                          _dp(force), int(threads), float(trt_lambda or 0.0), _dp(_mrt3(mrt)))
     if rc != 0:
         raise ValueError(f"or_run_faces failed with status {rc}")
     out = [p, u.reshape(d, N)]

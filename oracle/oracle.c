@@ -41,6 +41,18 @@
  *     omega and omega_m, Lambda = (1/omega - 1/2)(1/omega_m - 1/2); the Guo
  *     source splits the same way, its even half scaled by (1 - omega/2), its
  *     odd half by (1 - omega_m/2).  Lambda = 0 selects BGK.
+ *   - multiple-relaxation-time collision (not in the paper; d'Humieres et al.
+ *     2002): f*_a = f_a - sum_k M_ka [s_k m_k(f - feq) - (1 - s_k/2) m_k(S)]
+ *     / |M_k|^2 with m_k(g) = sum_a M_ka g_a, S the Guo source without its
+ *     (1 - omega/2) factor, and M the moment basis orthogonal over the
+ *     velocity set: the monomials e_x^i e_y^j e_z^k (i, j, k <= 2) taken by
+ *     degree, |e|^2 first among degree two, orthogonalised in that order
+ *     (Gram-Schmidt), linearly dependent ones dropped.  Rates by class:
+ *     density and momentum (conserved; any rate gives the same result), the
+ *     bulk row from |e|^2 at s_bulk, the other second-order rows (the
+ *     traceless stress) at omega, higher rows at s_even or s_odd by the
+ *     parity of their degree.  All rates = omega gives BGK; s_bulk = s_even
+ *     = omega and s_odd = omega_m give TRT.
  *   - per-face boundaries and obstacles (Sec. 4-5 use them; their discrete
  *     form is not printed): for the population entering fluid node x along
  *     e_a, take the upstream node x - e_a and fix each coordinate that
@@ -121,6 +133,9 @@ typedef struct {
     double lid[3];
     double omega, rho0;
     double omega_m; /* TRT odd-part rate; 0 = BGK */
+    int mrt;        /* MRT collision with the basis and rates below */
+    int nrow;       /* rows of the moment basis (= Q) */
+    double M[OR_MAXQ][OR_MAXQ], M2[OR_MAXQ], s_row[OR_MAXQ];
     int compressible;
     const double *F; /* d*N, component-major, or NULL */
 } or_model;
@@ -293,6 +308,95 @@ static void collide_node_trt(const or_model *m, const double *fn, const double *
     }
 }
 
+/* MRT collision (not in the paper): overwrites out[] with
+ *     f*_a = f_a - sum_k M_ka [s_k m_k(f - feq) - (1 - s_k/2) m_k(S)] / |M_k|^2. */
+static void collide_node_mrt(const or_model *m, const double *fn, const double *Fn,
+                             const double *feq, const double u[3], double *out)
+{
+    const or_dvm *v = &m->v;
+    double S[OR_MAXQ];
+    for (int a = 0; a < v->Q; ++a)
+        guo_source(v, a, u, Fn, &S[a]);
+    for (int a = 0; a < v->Q; ++a)
+        out[a] = fn[a];
+    for (int k = 0; k < m->nrow; ++k) {
+        double mn = 0.0, mS = 0.0;
+        for (int a = 0; a < v->Q; ++a) {
+            mn += m->M[k][a] * (fn[a] - feq[a]);
+            mS += m->M[k][a] * S[a];
+        }
+        const double ck = (m->s_row[k] * mn - (1.0 - 0.5 * m->s_row[k]) * mS) / m->M2[k];
+        for (int a = 0; a < v->Q; ++a)
+            out[a] -= ck * m->M[k][a];
+    }
+}
+
+/* The MRT moment basis and the rate of each row (see the header): monomials
+ * of degree 0, 1, 2 (|e|^2 first), 3, ... with exponents up to 2,
+ * orthogonalised over the velocity set in that order. */
+static int build_mrt(or_model *m, double s_bulk, double s_even, double s_odd)
+{
+    const or_dvm *v = &m->v;
+    const int D = v->d;
+    m->nrow = 0;
+    for (int deg = 0; deg <= 2 * D; ++deg) {
+        /* candidate vectors of this degree; code -1 = |e|^2 */
+        int npow = 1;
+        for (int k = 0; k < D; ++k)
+            npow *= 3;
+        for (int c = (deg == 2 ? -1 : 0); c < npow; ++c) {
+            int pw[3] = {0, 0, 0}, sum = 0;
+            if (c >= 0) {
+                int r = c;
+                for (int k = 0; k < D; ++k) {
+                    pw[k] = r % 3;
+                    r /= 3;
+                    sum += pw[k];
+                }
+                if (sum != deg)
+                    continue;
+            }
+            double w[OR_MAXQ];
+            for (int a = 0; a < v->Q; ++a) {
+                if (c < 0) {
+                    w[a] = 0.0;
+                    for (int k = 0; k < D; ++k)
+                        w[a] += v->e[a][k] * v->e[a][k];
+                } else {
+                    w[a] = 1.0;
+                    for (int k = 0; k < D; ++k)
+                        for (int i = 0; i < pw[k]; ++i)
+                            w[a] *= v->e[a][k];
+                }
+            }
+            for (int r = 0; r < m->nrow; ++r) {
+                double dot = 0.0;
+                for (int a = 0; a < v->Q; ++a)
+                    dot += w[a] * m->M[r][a];
+                for (int a = 0; a < v->Q; ++a)
+                    w[a] -= dot / m->M2[r] * m->M[r][a];
+            }
+            double n2 = 0.0;
+            for (int a = 0; a < v->Q; ++a)
+                n2 += w[a] * w[a];
+            if (n2 < 1e-9)
+                continue; /* dependent on the rows so far */
+            if (m->nrow >= v->Q)
+                return OR_ERR_ARG;
+            for (int a = 0; a < v->Q; ++a)
+                m->M[m->nrow][a] = w[a];
+            m->M2[m->nrow] = n2;
+            m->s_row[m->nrow] = deg <= 1    ? m->omega
+                                : c < 0     ? s_bulk
+                                : deg == 2  ? m->omega
+                                : deg % 2   ? s_odd
+                                            : s_even;
+            ++m->nrow;
+        }
+    }
+    return m->nrow == v->Q ? OR_OK : OR_ERR_ARG;
+}
+
 /* Eq. (collision): f*_a = f_a - omega (f_a - feq_a), omega = 1/(tau_p + 1/2)
  * = 1/tau_std, plus the Guo source in the same trapezoidal form. */
 static void collide_node(const or_model *m, const double *fn, const double *Fn,
@@ -315,6 +419,8 @@ static void collide_node(const or_model *m, const double *fn, const double *Fn,
     }
     if (m->omega_m > 0.0)
         collide_node_trt(m, fn, Fn, feq, u, out);
+    else if (m->mrt)
+        collide_node_mrt(m, fn, Fn, feq, u, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -633,7 +739,7 @@ static int faces_of_bc(int bc, int faces[6])
 
 static int setup_model(or_model *m, int lattice, int nx, int ny, int nz, double tau,
                        const int faces[6], int compressible, double rho0, const double *lid,
-                       const double *F, double trt_lambda)
+                       const double *F, double trt_lambda, const double *mrt)
 {
     memset(m, 0, sizeof(*m));
     if (build_dvm(lattice, &m->v) != OR_OK)
@@ -672,6 +778,16 @@ static int setup_model(or_model *m, int lattice, int nx, int ny, int nz, double 
     m->rho0 = rho0;
     m->compressible = compressible;
     m->F = F;
+    if (mrt) { /* rates s_bulk, s_even, s_odd in (0, 2); not with TRT */
+        for (int k = 0; k < 3; ++k)
+            if (!(mrt[k] > 0.0 && mrt[k] < 2.0))
+                return OR_ERR_ARG;
+        if (trt_lambda > 0.0)
+            return OR_ERR_ARG;
+        m->mrt = 1;
+        if (build_mrt(m, mrt[0], mrt[1], mrt[2]) != OR_OK)
+            return OR_ERR_ARG;
+    }
     return OR_OK;
 }
 
@@ -696,11 +812,11 @@ int or_run_faces(int lattice, int nx, int ny, int nz, double tau, const int *fac
                  const unsigned char *solid, const double *inlet_u, const double *p0,
                  const double *u0, double p_outflow, long nsteps, double *p_out,
                  double *u_out, double *f_out, double *force_out, int nthreads,
-                 double trt_lambda)
+                 double trt_lambda, const double *mrt)
 {
     or_model m;
     int rc = setup_model(&m, lattice, nx, ny, nz, tau, faces, compressible, rho0, lid, F,
-                         trt_lambda);
+                         trt_lambda, mrt);
     if (rc != OR_OK || nsteps < 0)
         return OR_ERR_ARG;
     int has_inlet = 0;
@@ -743,24 +859,24 @@ int or_run_faces(int lattice, int nx, int ny, int nz, double tau, const int *fac
 int or_run(int lattice, int nx, int ny, int nz, double tau, int bc, int compressible,
            double rho0, const double *lid, const double *F, const double *p0,
            const double *u0, long nsteps, double *p_out, double *u_out, double *f_out,
-           int nthreads, double trt_lambda)
+           int nthreads, double trt_lambda, const double *mrt)
 {
     int faces[6];
     if (faces_of_bc(bc, faces) != OR_OK)
         return OR_ERR_ARG;
     return or_run_faces(lattice, nx, ny, nz, tau, faces, compressible, rho0, lid, F, NULL,
                         NULL, p0, u0, 1.0 / INV_CS2, nsteps, p_out, u_out, f_out, NULL,
-                        nthreads, trt_lambda);
+                        nthreads, trt_lambda, mrt);
 }
 
 /* Exported: one collision at one node (tiny brute-force pins). */
 int or_collide_node(int lattice, double tau, int compressible, double rho0, const double *fn,
-                    const double *F3, double *out, double trt_lambda)
+                    const double *F3, double *out, double trt_lambda, const double *mrt)
 {
     or_model m;
     int faces[6] = {0, 0, 0, 0, 0, 0};
     int rc = setup_model(&m, lattice, 1, 1, 1, tau, faces, compressible, rho0, NULL, NULL,
-                         trt_lambda);
+                         trt_lambda, mrt);
     if (rc != OR_OK)
         return rc;
     collide_node(&m, fn, F3, out);
@@ -899,7 +1015,7 @@ int or_adjoint(int lattice, int nx, int ny, int nz, double tau, int bc, double r
     int faces[6];
     if (faces_of_bc(bc, faces) != OR_OK)
         return OR_ERR_ARG;
-    int rc = setup_model(&m, lattice, nx, ny, nz, tau, faces, 0, rho0, lid, F, 0.0);
+    int rc = setup_model(&m, lattice, nx, ny, nz, tau, faces, 0, rho0, lid, F, 0.0, NULL);
     if (rc != OR_OK || T < 1 || K < 1)
         return OR_ERR_ARG;
     set_threads(nthreads);

@@ -330,6 +330,94 @@ def test_trt_shear_viscosity_set_by_omega(lam):
     assert abs(rate / W.taylor_green_rate(n, n, tau) - 1) < 0.01
 
 
+@pytest.mark.parametrize("lattice", LATTICES)
+def test_mrt_reduces_to_bgk_and_trt(lattice):
+    """Multiple-relaxation-time collision: with every rate equal to omega it is
+    BGK, and with the even moments at omega and the odd ones at omega_m it is
+    TRT of the same Lambda (both pinned on their own elsewhere)."""
+    rng = np.random.default_rng(21)
+    e, t, _ = oracle.tables(lattice)
+    Q, d = oracle.dims(lattice)
+    for tau, lam in ((0.55, 3 / 16), (0.8, 1 / 4), (1.7, 1 / 12)):
+        om = 1 / tau
+        om_m = 1 / (lam / (tau - 0.5) + 0.5)
+        f = t * (1 + 0.05 * rng.standard_normal(Q))
+        F = 1e-4 * rng.standard_normal(d)
+        for Fx in (None, F):
+            bgk = oracle.collide_node(lattice, f, tau, F=Fx)
+            trt = oracle.collide_node(lattice, f, tau, F=Fx, trt_lambda=lam)
+            assert np.abs(oracle.collide_node(lattice, f, tau, F=Fx, mrt=(om, om, om)) -
+                          bgk).max() < 1e-15
+            assert np.abs(oracle.collide_node(lattice, f, tau, F=Fx, mrt=(om, om, om_m)) -
+                          trt).max() < 1e-15
+
+
+@pytest.mark.parametrize("lattice", LATTICES)
+def test_mrt_moments_relax_by_class(lattice):
+    """MRT keeps P and j (the force adds F), leaves feq fixed, relaxes the
+    non-equilibrium stress moments (e_x e_y, e_x^2 - e_y^2) at omega, the bulk
+    moment (|e|^2 minus its mean over the set) at s_bulk and odd third-order
+    moments (e_x e_y^2) at s_odd, whatever the other rates."""
+    rng = np.random.default_rng(22)
+    e, t, _ = oracle.tables(lattice)
+    Q, d = oracle.dims(lattice)
+    E = np.zeros((Q, 3))
+    E[:, :d] = e[:, :d]
+    c2 = (E ** 2).sum(axis=1)
+    for tau, rates in ((0.6, (1.5, 1.2, 1.1)), (1.3, (0.7, 1.9, 1.6))):
+        om = 1 / tau
+        sb, se, so = rates
+        f = t * (1 + 0.05 * rng.standard_normal(Q))
+        out = oracle.collide_node(lattice, f, tau, mrt=rates)
+        assert abs(out.sum() - f.sum()) < 1e-15
+        assert np.abs(E.T @ out - E.T @ f).max() < 1e-15
+        feq = oracle.equilibrium(lattice, f.sum(), (E.T @ f)[:d])
+        assert np.abs(oracle.collide_node(lattice, feq, tau, mrt=rates) - feq).max() < 1e-15
+        n, nout = f - feq, out - feq
+        for w, rate in ((E[:, 0] * E[:, 1], om), (E[:, 0] ** 2 - E[:, 1] ** 2, om),
+                        (c2 - c2.mean(), sb), (E[:, 0] * E[:, 1] ** 2, so)):
+            assert abs(w @ nout - (1 - rate) * (w @ n)) < 1e-15
+        F = 1e-4 * rng.standard_normal(d)
+        outF = oracle.collide_node(lattice, f, tau, F=F, mrt=rates)
+        assert abs(outF.sum() - f.sum()) < 1e-15
+        assert np.abs(E[:, :d].T @ outF - (E[:, :d].T @ f + F)).max() < 1e-15
+
+
+def test_mrt_shear_viscosity_set_by_omega():
+    """MRT: the shear-wave decay rate is nu (kx^2 + ky^2), nu = (tau - 1/2)/3,
+    from the stress rate alone, whatever the bulk and ghost rates (within 1 %)."""
+    n, tau = 96, 0.8
+    p0, u0 = W.taylor_green_2d(n, n, 0.05)
+    for rates in ((1.5, 1.2, 1.1), (0.9, 1.8, 1.4)):
+        amps = []
+        for T in (100, 900):
+            _, u = oracle.run("d2q9", n, n, 1, tau, "periodic", T, p0=p0, u0=u0, mrt=rates)
+            amps.append(_tg_amplitude(u, n))
+        rate = -math.log(amps[1] / amps[0]) / 800
+        assert abs(rate / W.taylor_green_rate(n, n, tau) - 1) < 0.01, rates
+
+
+def test_mrt_conserves_mass_and_momentum_on_periodic_box():
+    """Distinct MRT rates, D3Q19 periodic box: total mass and momentum stay
+    constant to rounding over 200 steps."""
+    nx, ny, nz = 12, 10, 8
+    p0, u0 = W.random_smooth_state(nx, ny, nz, 3, amp_u=0.04, seed=5)
+    _, _, f0 = oracle.run("d3q19", nx, ny, nz, 0.7, "periodic", 0, p0=p0, u0=u0.ravel(),
+                          want_f=True)
+    _, _, f1 = oracle.run("d3q19", nx, ny, nz, 0.7, "periodic", 200, p0=p0, u0=u0.ravel(),
+                          want_f=True, mrt=(1.4, 1.2, 1.1))
+    e, _, _ = oracle.tables("d3q19")
+    assert abs(f1.sum() - f0.sum()) < 1e-12 * f0.sum()
+    assert np.abs(e[:, :3].T @ f1.sum(axis=1) - e[:, :3].T @ f0.sum(axis=1)).max() < 1e-12
+
+
+def test_mrt_rates_are_checked():
+    f = oracle.equilibrium("d2q9", 1.0, [0.0, 0.0])
+    for bad in ((0.0, 1.0, 1.0), (1.0, 2.0, 1.0), (1.0, 1.0, float("nan"))):
+        with pytest.raises(AssertionError):
+            oracle.collide_node("d2q9", f, 0.8, mrt=bad)
+
+
 @pytest.mark.parametrize("lattice", ["d2q9", "d3q19"])
 def test_couette(lattice):
     """Moving top wall, no force: linear profile U (y + 1/2)/ny for any tau."""
