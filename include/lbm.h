@@ -126,8 +126,19 @@ typedef enum {
  * Lambda = 3/16 half-way bounce-back places Poiseuille walls exactly for
  * any tau, and Lambda = (tau - 1/2)^2 is BGK.  TRT is available with the
  * incompressible equilibrium only (compressible + TRT is LBM_ERR_ARG) and
+ * has no adjoint.
+ * MRT (multiple relaxation times, not in the paper; d'Humieres et al. 2002)
+ * relaxes the non-equilibrium part in an orthogonal moment basis (the
+ * monomials e_x^i e_y^j e_z^k, i, j, k <= 2, by degree with |e|^2 first
+ * among degree two, orthogonalised over the velocity set), with the Guo
+ * source transformed the same way: the traceless stress at omega = 1/tau
+ * (shear viscosity), the bulk moment (|e|^2) at mrt_bulk, the higher
+ * moments at mrt_even / mrt_odd by the parity of their degree; density and
+ * momentum are conserved (the force adds F).  A rate of 0 means omega, so
+ * the defaults are BGK.  MRT runs with the incompressible equilibrium and
+ * FP64 or FP32 storage (16-bit storage, compressible + MRT: LBM_ERR_ARG) and
  * has no adjoint. */
-typedef enum { LBM_COLL_BGK = 0, LBM_COLL_TRT = 1 } lbm_collision;
+typedef enum { LBM_COLL_BGK = 0, LBM_COLL_TRT = 1, LBM_COLL_MRT = 2 } lbm_collision;
 
 typedef struct {
     int storage;        /* lbm_storage */
@@ -142,13 +153,17 @@ typedef struct {
     int faces[6];       /* lbm_face per face (-x, +x, -y, +y, -z, +z), LBM_BC_FACES only */
     int geometry;       /* 1: solid obstacles will be set with lbm_set_geometry */
     double p_outflow;   /* pressure held at outflow faces (> 0, default 1/3) */
+    double mrt_bulk;    /* LBM_COLL_MRT: rate of the bulk moment, (0, 2), or 0 = omega */
+    double mrt_even;    /* LBM_COLL_MRT: rate of the even higher moments, (0, 2) or 0 */
+    double mrt_odd;     /* LBM_COLL_MRT: rate of the odd higher moments, (0, 2) or 0 */
 } lbm_opts;
 
 typedef struct lbm_ctx lbm_ctx;
 
 /* Defaults: LBM_F32, pull scheme, incompressible, BGK, shifted, rho0 = 1,
- * lid 0, trt_lambda 3/16 (used only with LBM_COLL_TRT), all faces periodic
- * (used only with LBM_BC_FACES), no obstacles, p_outflow 1/3. */
+ * lid 0, trt_lambda 3/16 (used only with LBM_COLL_TRT), MRT rates 0 (= omega),
+ * all faces periodic (used only with LBM_BC_FACES), no obstacles, p_outflow
+ * 1/3. */
 void lbm_default_opts(lbm_opts *opts);
 
 /* tau_std = tau_paper + 1/2 (Sec. 3.3: "ome = 1/(tau+0.5)"). */

@@ -55,11 +55,20 @@ bool valid_opts(const lbm_opts &o)
 {
     if (o.storage < LBM_F64 || o.storage > LBM_BF16S)
         return false;
-    if (o.collision != LBM_COLL_BGK && o.collision != LBM_COLL_TRT)
+    if (o.collision != LBM_COLL_BGK && o.collision != LBM_COLL_TRT &&
+        o.collision != LBM_COLL_MRT)
         return false;
     if (o.collision == LBM_COLL_TRT &&
         (o.compressible || !(o.trt_lambda > 0.0 && isfinite(o.trt_lambda))))
         return false;
+    if (o.collision == LBM_COLL_MRT) {
+        // incompressible model, FP64 / FP32 storage; each rate 0 (= omega) or in (0, 2)
+        if (o.compressible || (o.storage != LBM_F64 && o.storage != LBM_F32))
+            return false;
+        for (const double r : {o.mrt_bulk, o.mrt_even, o.mrt_odd})
+            if (!(r == 0.0 || (r > 0.0 && r < 2.0)))
+                return false;
+    }
     if (!(o.rho0 > 0.0) || !isfinite(o.rho0))
         return false;
     if (o.geometry != 0 && o.geometry != 1)
@@ -235,6 +244,12 @@ void fill_params(lbm_ctx *c)
     p.cd.kf_m = (1.0 - 0.5 * omega_m) / omega_m;
     p.cf.omega_m = (float)omega_m;
     p.cf.kf_m = (float)p.cd.kf_m;
+    // MRT rates of the bulk, even and odd higher moments (0: omega)
+    const double mrt[3] = {c->opts.mrt_bulk, c->opts.mrt_even, c->opts.mrt_odd};
+    for (int k = 0; k < 3; ++k) {
+        p.cd.mrt[k] = mrt[k] > 0.0 ? mrt[k] : omega;
+        p.cf.mrt[k] = (float)p.cd.mrt[k];
+    }
     p.cd.omega = omega;
     p.cd.rho0 = c->opts.rho0;
     p.cd.inv_rho0 = 1.0 / c->opts.rho0;
@@ -301,7 +316,10 @@ Launch base_launch(const lbm_ctx *c, int kind)
     l.kind = kind;
     l.storage = c->opts.storage;
     l.comp = c->opts.compressible != 0;
-    l.model = l.comp ? M_COMP : c->opts.collision == LBM_COLL_TRT ? M_TRT : M_INC;
+    l.model = l.comp                                   ? M_COMP
+              : c->opts.collision == LBM_COLL_TRT      ? M_TRT
+              : c->opts.collision == LBM_COLL_MRT      ? M_MRT
+                                                       : M_INC;
     l.force = c->force != nullptr;
     l.uout = false;
     l.sp = c->sp;

@@ -29,7 +29,7 @@ namespace lbm {
 enum Pattern { PAT_PULL = 0, PAT_GATHER = 1, PAT_LOCAL = 2 };
 // Collision model of a step kernel: incompressible BGK (the paper's),
 // compressible BGK, incompressible two-relaxation-time.
-enum Model { M_INC = 0, M_COMP = 1, M_TRT = 2 };
+enum Model { M_INC = 0, M_COMP = 1, M_TRT = 2, M_MRT = 3 };
 // Where post-collision populations f*_a(x) sit in the stored state.
 enum Form { FORM_LOCAL = 0, FORM_SWAPPED = 1, FORM_STREAMED = 2 };
 
@@ -47,6 +47,7 @@ struct Coef {
     R omega_m;   // TRT: relaxation rate of the antisymmetric part
     R kf_m;      // TRT: (1 - omega_m/2)/omega_m
     R lid[kMaxQ];  // 2 t_a rho0 (e_a . U)/c_s^2 for links crossing the moving wall
+    R mrt[3];      // MRT: rates of the bulk, even and odd higher moments
     R pout2;       // outflow: 2 (P_out - sigma)
     R pout_r;      // outflow: density of the even equilibrium (rho0, or P_out if compressible)
 };
@@ -149,6 +150,122 @@ __device__ __forceinline__ R wmul(R x)
         return o_mul(x, R(L::w(a)));
 }
 
+// Multiple-relaxation-time collision (not in the paper; d'Humieres et al.
+// 2002) on the moments of MrtBasis<L>, given the moments of collide():
+//     g*_a = g_a - sum_k M_ka [s_k m_k(n) - (1 - s_k/2) m_k(S)] / |M_k|^2,
+// n = g - feq (feq without the source), S the Guo source t_a [3 (e_a - u).F
+// + 9 (e_a.u)(e_a.F)].  The conserved rows add exactly F to the momentum
+// (their non-equilibrium moment is -F/2 whatever the rate), written here in
+// that closed form: + sum_k e_a,k F_k / |M_(1+k)|^2.
+template <class L, int r>
+__host__ __device__ constexpr int mrt_norm2()
+{
+    int n = 0;
+    for (int a = 0; a < L::Q; ++a)
+        n += MrtBasis<L>::M[r][a] * MrtBasis<L>::M[r][a];
+    return n;
+}
+template <class L, class R, bool FORCE>
+__device__ __forceinline__ void collide_mrt(R (&g)[L::Q], const R (&F)[3], const Coef<R> &c,
+                                            R s, R rho, R ir, const R (&jf)[3], const R (&u)[3])
+{
+    using B = MrtBasis<L>;
+    constexpr int Q = L::Q, H = Q / 2;
+    const R uu = o_fma(u[2], u[2], o_fma(u[1], u[1], o_mul(u[0], u[0])));
+    const R A = o_fma(o_mul(R(-1.5), rho), uu, s);
+    const R r3 = o_mul(R(3), rho), r45 = o_mul(R(4.5), rho);
+    R uF = R(0);
+    if constexpr (FORCE)
+        uF = o_fma(u[2], F[2], o_fma(u[1], F[1], o_mul(u[0], F[0])));
+    const R m3uF = o_mul(R(-3), uF);
+    R n[Q], G[Q];
+    SFor<0, H>::run([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        constexpr int b = opp<L>(a);
+        R ej = R(0), eF = R(0);
+        (void)eF;
+        SFor<0, 3>::run([&](auto K_) {
+            constexpr int k = decltype(K_)::value;
+            if constexpr (L::e(a, k) == 1) {
+                ej = o_add(ej, jf[k]);
+                if constexpr (FORCE)
+                    eF = o_add(eF, F[k]);
+            } else if constexpr (L::e(a, k) == -1) {
+                ej = o_sub(ej, jf[k]);
+                if constexpr (FORCE)
+                    eF = o_sub(eF, F[k]);
+            }
+        });
+        const R t = R(L::w(a));
+        const R eu = o_mul(ej, ir);
+        const R sym = o_fma(o_mul(r45, eu), eu, A), asym = o_mul(r3, eu);
+        n[a] = o_sub(g[a], o_mul(t, o_add(sym, asym)));
+        n[b] = o_sub(g[b], o_mul(t, o_sub(sym, asym)));
+        if constexpr (FORCE) {
+            const R gs = o_fma(o_mul(R(9), eu), eF, m3uF), ga = o_mul(R(3), eF);
+            G[a] = o_mul(t, o_add(gs, ga));
+            G[b] = o_mul(t, o_sub(gs, ga));
+        } else {
+            G[a] = G[b] = R(0);
+        }
+    });
+    n[H] = o_sub(g[H], o_mul(R(L::w(H)), A));
+    G[H] = FORCE ? o_mul(R(L::w(H)), m3uF) : R(0);
+    // coefficients of the non-conserved rows, then the update
+    R ck[Q];
+    SFor<L::D + 1, Q>::run([&](auto R_) {
+        constexpr int r = decltype(R_)::value;
+        R mn = R(0), mG = R(0);
+        (void)mG;
+        SFor<0, Q>::run([&](auto A_) {
+            constexpr int a = decltype(A_)::value;
+            constexpr int m = B::M[r][a];
+            if constexpr (m == 1) {
+                mn = o_add(mn, n[a]);
+                if constexpr (FORCE)
+                    mG = o_add(mG, G[a]);
+            } else if constexpr (m == -1) {
+                mn = o_sub(mn, n[a]);
+                if constexpr (FORCE)
+                    mG = o_sub(mG, G[a]);
+            } else if constexpr (m != 0) {
+                mn = o_fma(R(m), n[a], mn);
+                if constexpr (FORCE)
+                    mG = o_fma(R(m), G[a], mG);
+            }
+        });
+        constexpr int kind = B::kind[r];
+        const R rate = kind == 1 ? c.mrt[0] : kind == 2 ? c.omega : kind == 3 ? c.mrt[1] : c.mrt[2];
+        R v = o_mul(rate, mn);
+        if constexpr (FORCE)
+            v = o_fma(o_fma(R(-0.5), rate, R(1)), -mG, v);
+        ck[r] = o_mul(v, R(1.0 / mrt_norm2<L, r>()));
+    });
+    SFor<0, Q>::run([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        R ga = g[a];
+        SFor<L::D + 1, Q>::run([&](auto R_) {
+            constexpr int r = decltype(R_)::value;
+            constexpr int m = B::M[r][a];
+            if constexpr (m == 1)
+                ga = o_sub(ga, ck[r]);
+            else if constexpr (m == -1)
+                ga = o_add(ga, ck[r]);
+            else if constexpr (m != 0)
+                ga = o_fma(R(-m), ck[r], ga);
+        });
+        if constexpr (FORCE) {
+            SFor<0, L::D>::run([&](auto K_) {
+                constexpr int k = decltype(K_)::value;
+                constexpr int ek = L::e(a, k);
+                if constexpr (ek != 0)
+                    ga = o_fma(R(ek * (1.0 / mrt_norm2<L, 1 + k>())), F[k], ga);
+            });
+        }
+        g[a] = ga;
+    });
+}
+
 template <class L, class R, int MODEL, bool FORCE>
 __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coef<R> &c,
                                         R (&u)[3], R &s_out, R &rho_out)
@@ -193,6 +310,10 @@ __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coe
             jf[k] = j[k];
         u[k] = o_mul(jf[k], ir);
     });
+    if constexpr (MODEL == M_MRT) {
+        collide_mrt<L, R, FORCE>(g, F, c, s, rho, ir, jf, u);
+        return;
+    }
     const R uu = o_fma(u[2], u[2], o_fma(u[1], u[1], o_mul(u[0], u[0])));
     R A = o_fma(o_mul(R(-1.5), rho), uu, s);
     if constexpr (FORCE) {

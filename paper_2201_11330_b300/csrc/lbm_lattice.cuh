@@ -131,6 +131,119 @@ static_assert(check_set<D2Q9>(), "D2Q9 numbering");
 static_assert(check_set<D3Q19>(), "D3Q19 numbering");
 static_assert(check_set<D3Q27>(), "D3Q27 numbering");
 
+// ---- moment basis of the multiple-relaxation-time collision -----------------
+// Rows orthogonal over the velocity set: the monomials e_x^i e_y^j e_z^k
+// (i, j, k <= 2) by degree, |e|^2 first among degree two, orthogonalised in
+// that order and scaled to coprime integers (d'Humieres et al. 2002 build
+// theirs the same way).  kind: 0 density and momentum (conserved), 1 the
+// bulk row (from |e|^2), 2 the traceless stress, 3 / 4 the higher rows of
+// even / odd degree.  check_mrt verifies at compile time that the rows are
+// pairwise orthogonal, that row 0 is 1 and rows 1..D are the velocity
+// components, and the kinds' counts.
+template <class L>
+struct MrtBasis;
+template <>
+struct MrtBasis<D2Q9> {
+    static constexpr signed char kind[9] = {0, 0, 0, 1, 2, 2, 4, 4, 3};
+    static constexpr signed char M[9][9] = {
+        {1, 1, 1, 1, 1, 1, 1, 1, 1},
+        {-1, -1, -1, 0, 0, 0, 1, 1, 1},
+        {-1, 0, 1, -1, 0, 1, -1, 0, 1},
+        {2, -1, 2, -1, -4, -1, 2, -1, 2},
+        {0, 1, 0, -1, 0, -1, 0, 1, 0},
+        {1, 0, -1, 0, 0, 0, -1, 0, 1},
+        {-1, 0, 1, 2, 0, -2, -1, 0, 1},
+        {-1, 2, -1, 0, 0, 0, 1, -2, 1},
+        {1, -2, 1, -2, 4, -2, 1, -2, 1},
+    };
+};
+template <>
+struct MrtBasis<D3Q19> {
+    static constexpr signed char kind[19] = {0, 0, 0, 0, 1, 2, 2, 2, 2, 2, 4, 4, 4, 4, 4, 4, 3, 3, 3};
+    static constexpr signed char M[19][19] = {
+        {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1},
+        {-1, -1, -1, -1, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1},
+        {-1, 0, 0, 0, 1, -1, -1, -1, 0, 0, 0, 1, 1, 1, -1, 0, 0, 0, 1},
+        {0, -1, 0, 1, 0, -1, 0, 1, -1, 0, 1, -1, 0, 1, 0, -1, 0, 1, 0},
+        {8, 8, -11, 8, 8, 8, -11, 8, -11, -30, -11, 8, -11, 8, 8, 8, -11, 8, 8},
+        {1, 1, 2, 1, 1, -2, -1, -2, -1, 0, -1, -2, -1, -2, 1, 1, 2, 1, 1},
+        {1, 0, 0, 0, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, -1, 0, 0, 0, 1},
+        {0, 1, 0, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, -1, 0, 1, 0},
+        {1, -1, 0, -1, 1, 0, 1, 0, -1, 0, -1, 0, 1, 0, 1, -1, 0, -1, 1},
+        {0, 0, 0, 0, 0, 1, 0, -1, 0, 0, 0, -1, 0, 1, 0, 0, 0, 0, 0},
+        {-3, 0, 0, 0, 3, 2, 2, 2, 0, 0, 0, -2, -2, -2, -3, 0, 0, 0, 3},
+        {0, -3, 0, 3, 0, 2, 0, -2, 2, 0, -2, 2, 0, -2, 0, -3, 0, 3, 0},
+        {-3, 2, 2, 2, -3, 0, 0, 0, 0, 0, 0, 0, 0, 0, 3, -2, -2, -2, 3},
+        {0, -1, 2, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, -2, 1, 0},
+        {0, 0, 0, 0, 0, -1, 0, 1, 2, 0, -2, -1, 0, 1, 0, 0, 0, 0, 0},
+        {0, 0, 0, 0, 0, -1, 2, -1, 0, 0, 0, 1, -2, 1, 0, 0, 0, 0, 0},
+        {5, -2, -6, -2, 5, -2, -6, -2, 8, 4, 8, -2, -6, -2, 5, -2, -6, -2, 5},
+        {0, 3, -6, 3, 0, -2, 4, -2, -2, 4, -2, -2, 4, -2, 0, 3, -6, 3, 0},
+        {0, 0, 0, 0, 0, 1, -2, 1, -2, 4, -2, 1, -2, 1, 0, 0, 0, 0, 0},
+    };
+};
+template <>
+struct MrtBasis<D3Q27> {
+    static constexpr signed char kind[27] = {0, 0, 0, 0, 1, 2, 2, 2, 2, 2, 4, 4, 4, 4, 4, 4, 4, 3, 3, 3, 3, 3, 3, 4, 4, 4, 3};
+    static constexpr signed char M[27][27] = {
+        {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1},
+        {-1, -1, -1, -1, -1, -1, -1, -1, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1, 1},
+        {-1, -1, -1, 0, 0, 0, 1, 1, 1, -1, -1, -1, 0, 0, 0, 1, 1, 1, -1, -1, -1, 0, 0, 0, 1, 1, 1},
+        {-1, 0, 1, -1, 0, 1, -1, 0, 1, -1, 0, 1, -1, 0, 1, -1, 0, 1, -1, 0, 1, -1, 0, 1, -1, 0, 1},
+        {1, 0, 1, 0, -1, 0, 1, 0, 1, 0, -1, 0, -1, -2, -1, 0, -1, 0, 1, 0, 1, 0, -1, 0, 1, 0, 1},
+        {0, 1, 0, 1, 2, 1, 0, 1, 0, -2, -1, -2, -1, 0, -1, -2, -1, -2, 0, 1, 0, 1, 2, 1, 0, 1, 0},
+        {1, 1, 1, 0, 0, 0, -1, -1, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, -1, -1, -1, 0, 0, 0, 1, 1, 1},
+        {1, 0, -1, 1, 0, -1, 1, 0, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, -1, 0, 1, -1, 0, 1, -1, 0, 1},
+        {0, 1, 0, -1, 0, -1, 0, 1, 0, 0, 1, 0, -1, 0, -1, 0, 1, 0, 0, 1, 0, -1, 0, -1, 0, 1, 0},
+        {1, 0, -1, 0, 0, 0, -1, 0, 1, 1, 0, -1, 0, 0, 0, -1, 0, 1, 1, 0, -1, 0, 0, 0, -1, 0, 1},
+        {-1, -1, -1, 0, 0, 0, 1, 1, 1, 2, 2, 2, 0, 0, 0, -2, -2, -2, -1, -1, -1, 0, 0, 0, 1, 1, 1},
+        {-1, 0, 1, -1, 0, 1, -1, 0, 1, 2, 0, -2, 2, 0, -2, 2, 0, -2, -1, 0, 1, -1, 0, 1, -1, 0, 1},
+        {-1, -1, -1, 2, 2, 2, -1, -1, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, -2, -2, -2, 1, 1, 1},
+        {-1, 0, 1, 0, 0, 0, 1, 0, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, -1, 0, 0, 0, -1, 0, 1},
+        {-1, 2, -1, -1, 2, -1, -1, 2, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, -2, 1, 1, -2, 1, 1, -2, 1},
+        {-1, 0, 1, 2, 0, -2, -1, 0, 1, -1, 0, 1, 2, 0, -2, -1, 0, 1, -1, 0, 1, 2, 0, -2, -1, 0, 1},
+        {-1, 2, -1, 0, 0, 0, 1, -2, 1, -1, 2, -1, 0, 0, 0, 1, -2, 1, -1, 2, -1, 0, 0, 0, 1, -2, 1},
+        {1, 1, 1, -2, -2, -2, 1, 1, 1, -2, -2, -2, 4, 4, 4, -2, -2, -2, 1, 1, 1, -2, -2, -2, 1, 1, 1},
+        {1, 0, -1, 0, 0, 0, -1, 0, 1, -2, 0, 2, 0, 0, 0, 2, 0, -2, 1, 0, -1, 0, 0, 0, -1, 0, 1},
+        {1, -2, 1, 1, -2, 1, 1, -2, 1, -2, 4, -2, -2, 4, -2, -2, 4, -2, 1, -2, 1, 1, -2, 1, 1, -2, 1},
+        {1, 0, -1, -2, 0, 2, 1, 0, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, -1, 0, 1, 2, 0, -2, -1, 0, 1},
+        {1, -2, 1, 0, 0, 0, -1, 2, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, -1, 2, -1, 0, 0, 0, 1, -2, 1},
+        {1, -2, 1, -2, 4, -2, 1, -2, 1, 1, -2, 1, -2, 4, -2, 1, -2, 1, 1, -2, 1, -2, 4, -2, 1, -2, 1},
+        {-1, 0, 1, 2, 0, -2, -1, 0, 1, 2, 0, -2, -4, 0, 4, 2, 0, -2, -1, 0, 1, 2, 0, -2, -1, 0, 1},
+        {-1, 2, -1, 0, 0, 0, 1, -2, 1, 2, -4, 2, 0, 0, 0, -2, 4, -2, -1, 2, -1, 0, 0, 0, 1, -2, 1},
+        {-1, 2, -1, 2, -4, 2, -1, 2, -1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, -2, 1, -2, 4, -2, 1, -2, 1},
+        {1, -2, 1, -2, 4, -2, 1, -2, 1, -2, 4, -2, 4, -8, 4, -2, 4, -2, 1, -2, 1, -2, 4, -2, 1, -2, 1},
+    };
+};
+
+template <class L>
+constexpr bool check_mrt()
+{
+    using B = MrtBasis<L>;
+    for (int a = 0; a < L::Q; ++a) {
+        if (B::M[0][a] != 1)
+            return false;
+        for (int k = 0; k < L::D; ++k)
+            if (B::M[1 + k][a] != L::e(a, k))
+                return false;
+    }
+    int nkind[5] = {0, 0, 0, 0, 0};
+    for (int r = 0; r < L::Q; ++r) {
+        ++nkind[B::kind[r]];
+        for (int s = r + 1; s < L::Q; ++s) {
+            long dot = 0;
+            for (int a = 0; a < L::Q; ++a)
+                dot += (long)B::M[r][a] * B::M[s][a];
+            if (dot != 0)
+                return false;
+        }
+    }
+    return nkind[0] == L::D + 1 && nkind[1] == 1 && nkind[2] == (L::D == 3 ? 5 : 2);
+}
+static_assert(check_mrt<D2Q9>(), "D2Q9 moment basis");
+static_assert(check_mrt<D3Q19>(), "D3Q19 moment basis");
+static_assert(check_mrt<D3Q27>(), "D3Q27 moment basis");
+
 // Compile-time loop: f(std::integral_constant<int, I>) for I in [B, E).
 template <int B, int E>
 struct SFor {

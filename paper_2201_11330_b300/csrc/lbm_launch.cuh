@@ -29,6 +29,11 @@ inline cudaError_t with_model(int m, F &&f)
         return f(model_c<M_COMP>{});
     case M_TRT:
         return f(model_c<M_TRT>{});
+    case M_MRT:  // FP64 / FP32 storage only (the host refuses the rest)
+        if constexpr (S == ST_F64 || S == ST_F32)
+            return f(model_c<M_MRT>{});
+        else
+            return cudaErrorInvalidValue;
     default:
         return cudaErrorInvalidValue;
     }

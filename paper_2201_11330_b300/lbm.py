@@ -27,7 +27,7 @@ LBM_FACE_SYMMETRY, LBM_FACE_NODAL = 4, 5
 FACES = {"periodic": LBM_FACE_PERIODIC, "wall": LBM_FACE_WALL, "inlet": LBM_FACE_INLET,
          "outflow": LBM_FACE_OUTFLOW, "symmetry": LBM_FACE_SYMMETRY, "nodal": LBM_FACE_NODAL}
 LBM_F64, LBM_F32, LBM_F16S, LBM_BF16S = 0, 1, 2, 3
-LBM_COLL_BGK, LBM_COLL_TRT = 0, 1
+LBM_COLL_BGK, LBM_COLL_TRT, LBM_COLL_MRT = 0, 1, 2
 LBM_KERNEL_AUTO, LBM_KERNEL_PLAIN, LBM_KERNEL_PAIRED = 0, 1, 3
 KERNELS = {"auto": LBM_KERNEL_AUTO, "plain": LBM_KERNEL_PLAIN,
            "paired": LBM_KERNEL_PAIRED}
@@ -56,7 +56,8 @@ class lbm_opts(ctypes.Structure):
                 ("lid_u", ctypes.c_double * 3), ("has_force", ctypes.c_int),
                 ("collision", ctypes.c_int), ("trt_lambda", ctypes.c_double),
                 ("faces", ctypes.c_int * 6), ("geometry", ctypes.c_int),
-                ("p_outflow", ctypes.c_double)]
+                ("p_outflow", ctypes.c_double), ("mrt_bulk", ctypes.c_double),
+                ("mrt_even", ctypes.c_double), ("mrt_odd", ctypes.c_double)]
 
 
 class LBMError(RuntimeError):
@@ -299,12 +300,14 @@ class Lattice:
     "wall", "inlet", "outflow", "symmetry", "nodal"; order -x, +x, -y, +y,
     -z, +z).
     ``obstacles=True`` reserves the link words for ``set_geometry``.
+    ``mrt=(s_bulk, s_even, s_odd)`` selects the multiple-relaxation-time
+    collision with those rates (0 = 1/tau).
     """
 
     def __init__(self, lattice, nx, ny, nz, tau, bc, *, storage="f32", aa=False,
                  compressible=False, f32_unshifted=False, rho0=1.0, lid=(0.0, 0.0, 0.0),
                  has_force=False, kernel="auto", trt_lambda=None, obstacles=False,
-                 p_outflow=1.0 / 3.0, device="cuda"):
+                 p_outflow=1.0 / 3.0, mrt=None, device="cuda"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the LBM library needs a CUDA device")
@@ -340,6 +343,9 @@ class Lattice:
         if trt_lambda is not None:  # two-relaxation-time collision
             o.collision = LBM_COLL_TRT
             o.trt_lambda = float(trt_lambda)
+        if mrt is not None:  # multiple relaxation times: (bulk, even, odd) rates
+            o.collision = LBM_COLL_MRT
+            o.mrt_bulk, o.mrt_even, o.mrt_odd = (float(r) for r in mrt)
         self.opts = o
         nbytes = lbm_workspace_bytes(self.lattice, nx, ny, nz, o)
         if nbytes == 0:

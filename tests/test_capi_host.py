@@ -97,6 +97,27 @@ def test_create_validates_before_touching_memory(lib):
     o.trt_lambda = 3 / 16
     o.compressible = 1
     assert _create(lib, opts=o)[0] == lbm.LBM_ERR_ARG
+    # MRT: FP64 / FP32 storage, incompressible, rates 0 or in (0, 2)
+    o = lbm.lbm_default_opts()
+    o.collision = lbm.LBM_COLL_MRT
+    for st, rc in ((lbm.LBM_F64, lbm.LBM_OK), (lbm.LBM_F32, lbm.LBM_OK),
+                   (lbm.LBM_F16S, lbm.LBM_ERR_ARG), (lbm.LBM_BF16S, lbm.LBM_ERR_ARG)):
+        o.storage = st
+        r, ctx = _create(lib, opts=o)
+        assert r == rc, st
+        if r == lbm.LBM_OK:
+            lib.lbm_destroy(ctx)
+    o.storage = lbm.LBM_F32
+    o.compressible = 1
+    assert _create(lib, opts=o)[0] == lbm.LBM_ERR_ARG
+    o.compressible = 0
+    for bad in (2.0, -0.5, float("nan")):
+        o.mrt_odd = bad
+        assert _create(lib, opts=o)[0] == lbm.LBM_ERR_ARG
+    o.mrt_odd = 1.5
+    r, ctx = _create(lib, opts=o)
+    assert r == lbm.LBM_OK
+    lib.lbm_destroy(ctx)
     # the compressible model runs with every storage type
     o = lbm.lbm_default_opts()
     o.compressible = 1

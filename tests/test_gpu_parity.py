@@ -28,13 +28,13 @@ def _need_gpu():
 
 def gpu_run(lattice, shape, tau, bc, steps, *, storage="f64", aa=False, lid=None, F=None,
             p0=None, u0=None, compressible=False, rho0=1.0, f32_unshifted=False,
-            trt_lambda=None, kernel="auto"):
+            trt_lambda=None, kernel="auto", mrt=None):
     from paper_2201_11330_b300.lbm import Lattice
     nx, ny, nz = shape
     lat = Lattice(lattice, nx, ny, nz, tau, bc, storage=storage, aa=aa,
                   compressible=compressible, rho0=rho0, lid=lid or (0, 0, 0),
                   has_force=F is not None, f32_unshifted=f32_unshifted,
-                  trt_lambda=trt_lambda, kernel=kernel)
+                  trt_lambda=trt_lambda, kernel=kernel, mrt=mrt)
     if F is not None:
         lat.set_force(torch.from_numpy(np.ascontiguousarray(F, dtype=np.float32)).cuda())
     lat.init(None if p0 is None else torch.from_numpy(p0).cuda(),
@@ -47,12 +47,12 @@ def gpu_run(lattice, shape, tau, bc, steps, *, storage="f64", aa=False, lid=None
 
 
 def oracle_run(lattice, shape, tau, bc, steps, *, lid=None, F=None, p0=None, u0=None,
-               compressible=False, rho0=1.0, trt_lambda=None):
+               compressible=False, rho0=1.0, trt_lambda=None, mrt=None):
     nx, ny, nz = shape
     F64 = None if F is None else np.asarray(F, dtype=np.float32).astype(np.float64)
     return oracle.run(lattice, nx, ny, nz, tau, bc, steps, lid=lid, F=F64, p0=p0,
                       u0=None if u0 is None else np.ascontiguousarray(u0).ravel(),
-                      compressible=compressible, rho0=rho0, trt_lambda=trt_lambda)
+                      compressible=compressible, rho0=rho0, trt_lambda=trt_lambda, mrt=mrt)
 
 
 def errors(gpu, ref, uref, rho0=1.0):
