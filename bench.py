@@ -199,19 +199,24 @@ def timed_steps(lat, steps, warmup, world, per_launch=True):
     return total, durs, parity
 
 
-def make_cavity(lattice, n, re, storage, aa, lid_u=0.1, trt_lambda=None):
+# rates of the MRT benchmark line (bulk, even and odd higher moments)
+MRT_RATES = (1.19, 1.4, 1.2)
+
+
+def make_cavity(lattice, n, re, storage, aa, lid_u=0.1, trt_lambda=None, mrt=None):
     from paper_2201_11330_b300 import workloads as W
     from paper_2201_11330_b300.lbm import Lattice
     c = W.cavity_params(n, re, lid_u)
     lat = Lattice(lattice, n, n, n, c["tau"], "cavity", storage=storage, aa=aa, lid=c["lid"],
-                  trt_lambda=trt_lambda)
+                  trt_lambda=trt_lambda, mrt=mrt)
     lat.init()
     return lat
 
 
-def run_cavity(lattice, n, re, storage, aa, steps, warmup, world, device, trt_lambda=None):
+def run_cavity(lattice, n, re, storage, aa, steps, warmup, world, device, trt_lambda=None,
+               mrt=None):
     import torch
-    lat = make_cavity(lattice, n, re, storage, aa, trt_lambda=trt_lambda)
+    lat = make_cavity(lattice, n, re, storage, aa, trt_lambda=trt_lambda, mrt=mrt)
     total, durs, parity = timed_steps(lat, steps, warmup, world)
     total = max_over_ranks(total, world, device)
     N = n ** 3
@@ -219,7 +224,7 @@ def run_cavity(lattice, n, re, storage, aa, steps, warmup, world, device, trt_la
     bytes_per_node = 2 * Q_OF[lattice] * BYTES_OF[storage]
     out = {"glups": glups, "ms_per_step": total / steps, "bytes_per_node": bytes_per_node,
            "nodes": N}
-    tag = f"{lattice}_{storage}{'_trt' if trt_lambda else ''}"
+    tag = f"{lattice}_{storage}{'_trt' if trt_lambda else ''}{'_mrt' if mrt else ''}"
     if aa:
         g = [d for d, p in zip(durs, parity) if p == 0]
         l = [d for d, p in zip(durs, parity) if p == 1]
@@ -513,6 +518,9 @@ def main():
     ap.add_argument("--trt", action="store_true",
                     help="two-relaxation-time collision (Lambda = 3/16) for the headline run "
                          "(profiling)")
+    ap.add_argument("--mrt", action="store_true",
+                    help="multiple-relaxation-time collision (rates MRT_RATES) for the headline "
+                         "run (profiling)")
     ap.add_argument("--e2e", action="store_true",
                     help="with --no-extras: still run the two end-to-end legs (profiling)")
     ap.add_argument("--workload", default="cavity", choices=["cavity", "sphere"],
@@ -560,7 +568,8 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     head = run_cavity(hb["lattice"], hb["n"], hb["re"], hb["storage"], hb["aa"], args.steps,
-                      args.warmup, world, device, trt_lambda=3 / 16 if args.trt else None)
+                      args.warmup, world, device, trt_lambda=3 / 16 if args.trt else None,
+                      mrt=MRT_RATES if args.mrt else None)
     clocks = sampler.stop()
 
     N = head["nodes"]
@@ -576,7 +585,8 @@ def main():
         pat = "PULL"
     dom_name = f"k_step<{lat_tag},{st_tag},{pat}>"
     achieved = N * bpn / (dom_ms * 1e-3) / 1e9
-    traffic = load_traffic(f"{hb['lattice']}_{hb['storage']}{'_trt' if args.trt else ''}_"
+    traffic = load_traffic(f"{hb['lattice']}_{hb['storage']}{'_trt' if args.trt else ''}"
+                           f"{'_mrt' if args.mrt else ''}_"
                            f"{pat.lower()}_{hb['n']}")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
@@ -602,6 +612,11 @@ def main():
                            device, trt_lambda=3 / 16)
             r["hbm_frac"] = r["glups"] / world * r["bytes_per_node"] / peak
             extras[f"d3q19_{st}_aa_trt"] = r
+        # multiple-relaxation-time collision, FP32 storage
+        r = run_cavity("d3q19", hb["n"], hb["re"], "f32", True, args.steps, args.warmup, world,
+                       device, mrt=MRT_RATES)
+        r["hbm_frac"] = r["glups"] / world * r["bytes_per_node"] / peak
+        extras["d3q19_f32_aa_mrt"] = r
         n27 = 768 if hb["n"] == 512 else hb["n"]
         r = run_cavity("d3q27", n27, 2000.0, "f16s", True, max(10, args.steps // 4),
                        args.warmup, world, device)
