@@ -151,12 +151,17 @@ __device__ __forceinline__ R wmul(R x)
 }
 
 // Multiple-relaxation-time collision (not in the paper; d'Humieres et al.
-// 2002) on the moments of MrtBasis<L>, given the moments of collide():
+// 2002) on the moments of MrtBasis<L>:
 //     g*_a = g_a - sum_k M_ka [s_k m_k(n) - (1 - s_k/2) m_k(S)] / |M_k|^2,
 // n = g - feq (feq without the source), S the Guo source t_a [3 (e_a - u).F
-// + 9 (e_a.u)(e_a.F)].  The conserved rows add exactly F to the momentum
-// (their non-equilibrium moment is -F/2 whatever the rate), written here in
-// that closed form: + sum_k e_a,k F_k / |M_(1+k)|^2.
+// + 9 (e_a.u)(e_a.F)].  Summed over a complete orthogonal basis with every
+// s_k = omega this is the BGK update, so
+//     g* = BGK(g) + sum_k M_ka (omega - s_k) [m_k(n) + m_k(S)/2] / |M_k|^2
+// over the rows whose rate differs from omega: the bulk and the higher rows
+// (the stress relaxes at omega; density and momentum at any rate give the
+// same result, omega here).  mrt_corrections returns those coefficients,
+// computed from the pre-collision g; collide() applies them after its BGK
+// pass.  With every rate equal to omega the corrections vanish exactly.
 template <class L, int r>
 __host__ __device__ constexpr int mrt_norm2()
 {
@@ -166,8 +171,10 @@ __host__ __device__ constexpr int mrt_norm2()
     return n;
 }
 template <class L, class R, bool FORCE>
-__device__ __forceinline__ void collide_mrt(R (&g)[L::Q], const R (&F)[3], const Coef<R> &c,
-                                            R s, R rho, R ir, const R (&jf)[3], const R (&u)[3])
+__device__ __forceinline__ void mrt_corrections(const R (&g)[L::Q], const R (&F)[3],
+                                                const Coef<R> &c, R s, R rho, R ir,
+                                                const R (&jf)[3], const R (&u)[3],
+                                                R (&ck)[L::Q])
 {
     using B = MrtBasis<L>;
     constexpr int Q = L::Q, H = Q / 2;
@@ -178,7 +185,8 @@ __device__ __forceinline__ void collide_mrt(R (&g)[L::Q], const R (&F)[3], const
     if constexpr (FORCE)
         uF = o_fma(u[2], F[2], o_fma(u[1], F[1], o_mul(u[0], F[0])));
     const R m3uF = o_mul(R(-3), uF);
-    R n[Q], G[Q];
+    // h = n + S/2, the only combination the corrections need
+    R h[Q];
     SFor<0, H>::run([&](auto A_) {
         constexpr int a = decltype(A_)::value;
         constexpr int b = opp<L>(a);
@@ -198,70 +206,64 @@ __device__ __forceinline__ void collide_mrt(R (&g)[L::Q], const R (&F)[3], const
         });
         const R t = R(L::w(a));
         const R eu = o_mul(ej, ir);
-        const R sym = o_fma(o_mul(r45, eu), eu, A), asym = o_mul(r3, eu);
-        n[a] = o_sub(g[a], o_mul(t, o_add(sym, asym)));
-        n[b] = o_sub(g[b], o_mul(t, o_sub(sym, asym)));
-        if constexpr (FORCE) {
-            const R gs = o_fma(o_mul(R(9), eu), eF, m3uF), ga = o_mul(R(3), eF);
-            G[a] = o_mul(t, o_add(gs, ga));
-            G[b] = o_mul(t, o_sub(gs, ga));
-        } else {
-            G[a] = G[b] = R(0);
+        R sym = o_fma(o_mul(r45, eu), eu, A), asym = o_mul(r3, eu);
+        if constexpr (FORCE) {  // feq - S/2: S/2 = t [(9 eu eF - 3 uF)/2 +- 3 eF/2]
+            sym = o_fma(o_mul(R(-4.5), eu), eF, o_fma(R(-0.5), m3uF, sym));
+            asym = o_fma(R(-1.5), eF, asym);
         }
+        h[a] = o_sub(g[a], o_mul(t, o_add(sym, asym)));
+        h[b] = o_sub(g[b], o_mul(t, o_sub(sym, asym)));
     });
-    n[H] = o_sub(g[H], o_mul(R(L::w(H)), A));
-    G[H] = FORCE ? o_mul(R(L::w(H)), m3uF) : R(0);
-    // coefficients of the non-conserved rows, then the update
-    R ck[Q];
+    {
+        R a0 = A;
+        if constexpr (FORCE)
+            a0 = o_fma(R(-0.5), m3uF, a0);
+        h[H] = o_sub(g[H], o_mul(R(L::w(H)), a0));
+    }
     SFor<L::D + 1, Q>::run([&](auto R_) {
         constexpr int r = decltype(R_)::value;
-        R mn = R(0), mG = R(0);
-        (void)mG;
-        SFor<0, Q>::run([&](auto A_) {
-            constexpr int a = decltype(A_)::value;
-            constexpr int m = B::M[r][a];
-            if constexpr (m == 1) {
-                mn = o_add(mn, n[a]);
-                if constexpr (FORCE)
-                    mG = o_add(mG, G[a]);
-            } else if constexpr (m == -1) {
-                mn = o_sub(mn, n[a]);
-                if constexpr (FORCE)
-                    mG = o_sub(mG, G[a]);
-            } else if constexpr (m != 0) {
-                mn = o_fma(R(m), n[a], mn);
-                if constexpr (FORCE)
-                    mG = o_fma(R(m), G[a], mG);
-            }
-        });
         constexpr int kind = B::kind[r];
-        const R rate = kind == 1 ? c.mrt[0] : kind == 2 ? c.omega : kind == 3 ? c.mrt[1] : c.mrt[2];
-        R v = o_mul(rate, mn);
-        if constexpr (FORCE)
-            v = o_fma(o_fma(R(-0.5), rate, R(1)), -mG, v);
-        ck[r] = o_mul(v, R(1.0 / mrt_norm2<L, r>()));
+        if constexpr (kind == 2) {  // the stress: at omega, no correction
+            ck[r] = R(0);
+        } else {
+            R mh = R(0);
+            SFor<0, Q>::run([&](auto A_) {
+                constexpr int a = decltype(A_)::value;
+                constexpr int m = B::M[r][a];
+                if constexpr (m == 1)
+                    mh = o_add(mh, h[a]);
+                else if constexpr (m == -1)
+                    mh = o_sub(mh, h[a]);
+                else if constexpr (m != 0)
+                    mh = o_fma(R(m), h[a], mh);
+            });
+            const R rate = kind == 1 ? c.mrt[0] : kind == 3 ? c.mrt[1] : c.mrt[2];
+            ck[r] = o_mul(o_mul(o_sub(c.omega, rate), mh), R(1.0 / mrt_norm2<L, r>()));
+        }
     });
+}
+
+// g_a += sum_k M_ka ck_k over the rows that carry a correction.
+template <class L, class R>
+__device__ __forceinline__ void mrt_apply(R (&g)[L::Q], const R (&ck)[L::Q])
+{
+    using B = MrtBasis<L>;
+    constexpr int Q = L::Q;
     SFor<0, Q>::run([&](auto A_) {
         constexpr int a = decltype(A_)::value;
         R ga = g[a];
         SFor<L::D + 1, Q>::run([&](auto R_) {
             constexpr int r = decltype(R_)::value;
             constexpr int m = B::M[r][a];
-            if constexpr (m == 1)
-                ga = o_sub(ga, ck[r]);
-            else if constexpr (m == -1)
-                ga = o_add(ga, ck[r]);
-            else if constexpr (m != 0)
-                ga = o_fma(R(-m), ck[r], ga);
+            if constexpr (B::kind[r] != 2) {
+                if constexpr (m == 1)
+                    ga = o_add(ga, ck[r]);
+                else if constexpr (m == -1)
+                    ga = o_sub(ga, ck[r]);
+                else if constexpr (m != 0)
+                    ga = o_fma(R(m), ck[r], ga);
+            }
         });
-        if constexpr (FORCE) {
-            SFor<0, L::D>::run([&](auto K_) {
-                constexpr int k = decltype(K_)::value;
-                constexpr int ek = L::e(a, k);
-                if constexpr (ek != 0)
-                    ga = o_fma(R(ek * (1.0 / mrt_norm2<L, 1 + k>())), F[k], ga);
-            });
-        }
         g[a] = ga;
     });
 }
@@ -310,10 +312,10 @@ __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coe
             jf[k] = j[k];
         u[k] = o_mul(jf[k], ir);
     });
-    if constexpr (MODEL == M_MRT) {
-        collide_mrt<L, R, FORCE>(g, F, c, s, rho, ir, jf, u);
-        return;
-    }
+    R ck[L::Q];  // MRT: corrections to the BGK update (from the pre-collision g)
+    (void)ck;
+    if constexpr (MODEL == M_MRT)
+        mrt_corrections<L, R, FORCE>(g, F, c, s, rho, ir, jf, u, ck);
     const R uu = o_fma(u[2], u[2], o_fma(u[1], u[1], o_mul(u[0], u[0])));
     R A = o_fma(o_mul(R(-1.5), rho), uu, s);
     if constexpr (FORCE) {
@@ -394,6 +396,8 @@ __device__ __forceinline__ void collide(R (&g)[L::Q], const R (&F)[3], const Coe
         const R t0 = R(L::w(H));
         g[H] = o_fma(om, o_fma(t0, A, -g[H]), g[H]);
     }
+    if constexpr (MODEL == M_MRT)
+        mrt_apply<L, R>(g, ck);
 }
 
 // ---- neighbours -------------------------------------------------------------
