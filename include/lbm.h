@@ -135,9 +135,9 @@ typedef enum {
  * (shear viscosity), the bulk moment (|e|^2) at mrt_bulk, the higher
  * moments at mrt_even / mrt_odd by the parity of their degree; density and
  * momentum are conserved (the force adds F).  A rate of 0 means omega, so
- * the defaults are BGK.  MRT runs with the incompressible equilibrium
- * (compressible + MRT: LBM_ERR_ARG) and has no adjoint; with 16-bit storage
- * it runs on the one-node kernel (LBM_KERNEL_PAIRED is LBM_ERR_ARG). */
+ * the defaults are BGK.  MRT runs with the incompressible equilibrium and
+ * FP64 or FP32 storage (16-bit storage, compressible + MRT: LBM_ERR_ARG) and
+ * has no adjoint. */
 typedef enum { LBM_COLL_BGK = 0, LBM_COLL_TRT = 1, LBM_COLL_MRT = 2 } lbm_collision;
 
 typedef struct {

@@ -62,8 +62,8 @@ bool valid_opts(const lbm_opts &o)
         (o.compressible || !(o.trt_lambda > 0.0 && isfinite(o.trt_lambda))))
         return false;
     if (o.collision == LBM_COLL_MRT) {
-        // incompressible model; each rate 0 (= omega) or in (0, 2)
-        if (o.compressible)
+        // incompressible model, FP64 / FP32 storage; each rate 0 (= omega) or in (0, 2)
+        if (o.compressible || (o.storage != LBM_F64 && o.storage != LBM_F32))
             return false;
         for (const double r : {o.mrt_bulk, o.mrt_even, o.mrt_odd})
             if (!(r == 0.0 || (r > 0.0 && r < 2.0)))
@@ -292,8 +292,7 @@ void keep_inlet(lbm_ctx *c, const float *inlet) { c->sp.inlet = inlet; }
 // The paired kernel moves two 16-bit values per thread and slot.
 bool pair_eligible(const lbm_ctx *c)
 {
-    return (c->opts.storage == LBM_F16S || c->opts.storage == LBM_BF16S) && c->nx % 2 == 0 &&
-           c->opts.collision != LBM_COLL_MRT;  // its packed collision has no MRT form
+    return (c->opts.storage == LBM_F16S || c->opts.storage == LBM_BF16S) && c->nx % 2 == 0;
 }
 
 bool use_pair(const lbm_ctx *c, int pattern = PAT_PULL)

@@ -29,8 +29,11 @@ inline cudaError_t with_model(int m, F &&f)
         return f(model_c<M_COMP>{});
     case M_TRT:
         return f(model_c<M_TRT>{});
-    case M_MRT:  // the one-node kernels only (the paired kernel has no MRT form)
-        return f(model_c<M_MRT>{});
+    case M_MRT:  // FP64 / FP32 storage only (the host refuses the rest)
+        if constexpr (S == ST_F64 || S == ST_F32)
+            return f(model_c<M_MRT>{});
+        else
+            return cudaErrorInvalidValue;
     default:
         return cudaErrorInvalidValue;
     }
@@ -59,9 +62,6 @@ cudaError_t launch_storage(const Launch &l)
                 return with_bool(l.force, [&](auto Fo) {
                     constexpr int c = decltype(C)::value;
                     constexpr bool fo = decltype(Fo)::value;
-                    if constexpr (c == M_MRT) {
-                        return cudaErrorInvalidValue;  // never paired (use_pair)
-                    } else {
                     const auto *s16 = (const unsigned short *)l.src;
                     auto *d16 = (unsigned short *)l.dst;
                     return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
@@ -90,7 +90,6 @@ cudaError_t launch_storage(const Launch &l)
                             go(integral_constant<int, PAT_LOCAL>{}, integral_constant<int, mb_local>{});
                         return cudaGetLastError();
                     });
-                    }
                 });
             });
         } else {
@@ -126,7 +125,7 @@ cudaError_t launch_storage(const Launch &l)
             return with_bool(l.force, [&](auto Fo) {
                 constexpr int c = decltype(C)::value;
                 constexpr bool fo = decltype(Fo)::value;
-                if constexpr ((S == ST_F16S || S == ST_BF16S) && c != M_MRT) {
+                if constexpr (S == ST_F16S || S == ST_BF16S) {
                     if (l.pair) {
                         const auto *s16 = (const unsigned short *)l.src;
                         auto *d16 = (unsigned short *)l.dst;

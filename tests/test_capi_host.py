@@ -97,11 +97,11 @@ def test_create_validates_before_touching_memory(lib):
     o.trt_lambda = 3 / 16
     o.compressible = 1
     assert _create(lib, opts=o)[0] == lbm.LBM_ERR_ARG
-    # MRT: every storage type, incompressible, rates 0 or in (0, 2)
+    # MRT: FP64 / FP32 storage, incompressible, rates 0 or in (0, 2)
     o = lbm.lbm_default_opts()
     o.collision = lbm.LBM_COLL_MRT
     for st, rc in ((lbm.LBM_F64, lbm.LBM_OK), (lbm.LBM_F32, lbm.LBM_OK),
-                   (lbm.LBM_F16S, lbm.LBM_OK), (lbm.LBM_BF16S, lbm.LBM_OK)):
+                   (lbm.LBM_F16S, lbm.LBM_ERR_ARG), (lbm.LBM_BF16S, lbm.LBM_ERR_ARG)):
         o.storage = st
         r, ctx = _create(lib, opts=o)
         assert r == rc, st
