@@ -2,5 +2,7 @@
 #include "lbm_launch.cuh"
 
 namespace lbm {
+// the MRT launches are instantiated in lbm_d2q9_f64_mrt.cu
+extern template cudaError_t launch_mrt<D2Q9, ST_F64>(const Launch &);
 cudaError_t launch_d2q9_f64(const Launch &l) { return launch_storage<D2Q9, ST_F64>(l); }
 }  // namespace lbm

@@ -2,5 +2,7 @@
 #include "lbm_launch.cuh"
 
 namespace lbm {
+// the MRT launches are instantiated in lbm_d3q19_f32_mrt.cu
+extern template cudaError_t launch_mrt<D3Q19, ST_F32>(const Launch &);
 cudaError_t launch_d3q19_f32(const Launch &l) { return launch_storage<D3Q19, ST_F32>(l); }
 }  // namespace lbm

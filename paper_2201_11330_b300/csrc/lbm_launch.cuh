@@ -18,26 +18,37 @@ inline cudaError_t with_bool(bool b, F &&f)
 template <int M>
 using model_c = std::integral_constant<int, M>;
 
-// one instantiation per collision model (Model)
-template <int S, class F>
+// One instantiation per collision model (Model).  PART 0: every model but
+// MRT; PART 1: MRT only (FP64 / FP32 storage; the host refuses the rest).  The
+// MRT kernels are instantiated in translation units of their own
+// (lbm_<lattice>_<storage>_mrt.cu), which compile in parallel with the rest.
+template <int S, int PART, class F>
 inline cudaError_t with_model(int m, F &&f)
 {
-    switch (m) {
-    case M_INC:
-        return f(model_c<M_INC>{});
-    case M_COMP:
-        return f(model_c<M_COMP>{});
-    case M_TRT:
-        return f(model_c<M_TRT>{});
-    case M_MRT:  // FP64 / FP32 storage only (the host refuses the rest)
-        if constexpr (S == ST_F64 || S == ST_F32)
-            return f(model_c<M_MRT>{});
-        else
-            return cudaErrorInvalidValue;
-    default:
+    if constexpr (PART == 1) {
+        if constexpr (S == ST_F64 || S == ST_F32) {
+            if (m == M_MRT)
+                return f(model_c<M_MRT>{});
+        }
         return cudaErrorInvalidValue;
+    } else {
+        switch (m) {
+        case M_INC:
+            return f(model_c<M_INC>{});
+        case M_COMP:
+            return f(model_c<M_COMP>{});
+        case M_TRT:
+            return f(model_c<M_TRT>{});
+        default:
+            return cudaErrorInvalidValue;
+        }
     }
 }
+
+// The step and initialisation launches of the MRT model (PART 1 of
+// launch_storage), defined in lbm_<lattice>_<storage>_mrt.cu.
+template <class L, int S>
+cudaError_t launch_mrt(const Launch &l);
 
 // plain D3Q27 pull / gather kernels with 16-bit storage: blocks per SM bound
 template <class L, int S>
@@ -49,16 +60,24 @@ constexpr int kPlainGatherMinBlocks = kPlainMinBlocks<L, S> > 0 ? kPlainMinBlock
                                       : (L::Q == 27 && S == ST_F32) ? 3
                                                                     : 0;
 
-template <class L, int S>
+// MRT step kernels: blocks per SM bound per pattern (0: the thread bound alone)
+template <class L, int S, int PAT>
+constexpr int kMrtMinBlocks = 0;
+
+template <class L, int S, int PART = 0>
 cudaError_t launch_storage(const Launch &l)
 {
     using T = typename Sto<S>::T;
     const T *src = (const T *)l.src;
     T *dst = (T *)l.dst;
+    if constexpr (PART == 0 && (S == ST_F64 || S == ST_F32)) {
+        if ((l.kind == K_STEP || l.kind == K_INIT) && l.model == M_MRT)
+            return launch_mrt<L, S>(l);
+    }
     if (l.kind == K_STEP && l.pair && !l.skip) {
         if constexpr (S == ST_F16S || S == ST_BF16S) {
             const dim3 grid((l.sp.nx + 2 * kPairThreads - 1) / (2 * kPairThreads), l.sp.ny, l.sp.nz);
-            return with_model<S>(l.model, [&](auto C) {
+            return with_model<S, PART>(l.model, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
                     constexpr int c = decltype(C)::value;
                     constexpr bool fo = decltype(Fo)::value;
@@ -97,7 +116,7 @@ cudaError_t launch_storage(const Launch &l)
         }
     }
     if (l.kind == K_STEP && l.geo) {
-        return with_model<S>(l.model, [&](auto C) {
+        return with_model<S, PART>(l.model, [&](auto C) {
             return with_bool(l.force, [&](auto Fo) {
                 constexpr int c = decltype(C)::value;
                 constexpr bool fo = decltype(Fo)::value;
@@ -121,7 +140,7 @@ cudaError_t launch_storage(const Launch &l)
         });
     }
     if (l.kind == K_STEP && l.skip) {
-        return with_model<S>(l.model, [&](auto C) {
+        return with_model<S, PART>(l.model, [&](auto C) {
             return with_bool(l.force, [&](auto Fo) {
                 constexpr int c = decltype(C)::value;
                 constexpr bool fo = decltype(Fo)::value;
@@ -151,38 +170,46 @@ cudaError_t launch_storage(const Launch &l)
             });
         });
     }
-    if (l.kind == K_FLAGS) {
-        if constexpr (S == ST_F32) {  // storage-independent: one instantiation per lattice
-            k_node_flags<L><<<l.grid, l.block, 0, l.stream>>>(l.flags, l.sp, l.pair);
-            return cudaGetLastError();
-        } else {
-            return cudaErrorInvalidValue;
+    if constexpr (PART == 0) {  // model-independent kernels: not in the MRT units
+        if (l.kind == K_FLAGS) {
+            if constexpr (S == ST_F32) {  // storage-independent: one instantiation per lattice
+                k_node_flags<L><<<l.grid, l.block, 0, l.stream>>>(l.flags, l.sp, l.pair);
+                return cudaGetLastError();
+            } else {
+                return cudaErrorInvalidValue;
+            }
         }
-    }
-    if (l.kind == K_LINKS) {
-        if constexpr (S == ST_F32) {  // storage-independent: one instantiation per lattice
-            k_links<L><<<l.grid, l.block, 0, l.stream>>>(l.solid, l.links, l.nsolid, l.sp);
-            return cudaGetLastError();
-        } else {
-            return cudaErrorInvalidValue;
+        if (l.kind == K_LINKS) {
+            if constexpr (S == ST_F32) {  // storage-independent: one instantiation per lattice
+                k_links<L><<<l.grid, l.block, 0, l.stream>>>(l.solid, l.links, l.nsolid, l.sp);
+                return cudaGetLastError();
+            } else {
+                return cudaErrorInvalidValue;
+            }
         }
     }
     if (l.kind == K_STEP) {
         if (l.pattern == PAT_PULL) {
-            if (l.uout) {
-                // adjoint recompute: incompressible BGK only
-                return with_bool(l.force, [&](auto Fo) {
-                    k_step<L, S, PAT_PULL, M_INC, decltype(Fo)::value, true>
-                        <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
-                    return cudaGetLastError();
-                });
+            if constexpr (PART == 0) {
+                if (l.uout) {
+                    // adjoint recompute: incompressible BGK only
+                    return with_bool(l.force, [&](auto Fo) {
+                        k_step<L, S, PAT_PULL, M_INC, decltype(Fo)::value, true>
+                            <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                        return cudaGetLastError();
+                    });
+                }
             }
-            return with_model<S>(l.model, [&](auto C) {
+            return with_model<S, PART>(l.model, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
                     return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
                         constexpr int c = decltype(C)::value;
                         constexpr bool fo = decltype(Fo)::value, rd = decltype(Rd)::value;
-                        if constexpr (kPlainMinBlocks<L, S> > 0 && !rd)
+                        constexpr int mrt_mb = c == M_MRT ? kMrtMinBlocks<L, S, PAT_PULL> : 0;
+                        if constexpr (mrt_mb > 0 && !rd)
+                            k_step_bounded<L, S, PAT_PULL, c, fo, mrt_mb>
+                                <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                        else if constexpr (kPlainMinBlocks<L, S> > 0 && !rd)
                             k_step_bounded<L, S, PAT_PULL, c, fo, kPlainMinBlocks<L, S>>
                                 <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
                         else
@@ -194,13 +221,17 @@ cudaError_t launch_storage(const Launch &l)
             });
         }
         if (l.pattern == PAT_GATHER) {
-            return with_model<S>(l.model, [&](auto C) {
+            return with_model<S, PART>(l.model, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
                     constexpr int c = decltype(C)::value;
                     constexpr bool fo = decltype(Fo)::value;
+                    constexpr int mrt_mb = c == M_MRT ? kMrtMinBlocks<L, S, PAT_GATHER> : 0;
                     if (l.sp.partials != nullptr)
                         k_step_gather_red<L, S, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, dst,
                                                                                          l.sp);
+                    else if constexpr (mrt_mb > 0)
+                        k_step_bounded<L, S, PAT_GATHER, c, fo, mrt_mb>
+                            <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
                     else if constexpr (kPlainGatherMinBlocks<L, S> > 0)
                         k_step_bounded<L, S, PAT_GATHER, c, fo, kPlainGatherMinBlocks<L, S>>
                             <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
@@ -211,11 +242,18 @@ cudaError_t launch_storage(const Launch &l)
                 });
             });
         }
-        return with_model<S>(l.model, [&](auto C) {
+        return with_model<S, PART>(l.model, [&](auto C) {
             return with_bool(l.force, [&](auto Fo) {
                 return with_bool(l.sp.partials != nullptr, [&](auto Rd) {
-                    k_step<L, S, PAT_LOCAL, decltype(C)::value, decltype(Fo)::value, false,
-                           decltype(Rd)::value><<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                    constexpr int c = decltype(C)::value;
+                    constexpr bool fo = decltype(Fo)::value, rd = decltype(Rd)::value;
+                    constexpr int mrt_mb = c == M_MRT ? kMrtMinBlocks<L, S, PAT_LOCAL> : 0;
+                    if constexpr (mrt_mb > 0 && !rd)
+                        k_step_bounded<L, S, PAT_LOCAL, c, fo, mrt_mb>
+                            <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
+                    else
+                        k_step<L, S, PAT_LOCAL, c, fo, false, rd>
+                            <<<l.grid, l.block, 0, l.stream>>>(src, dst, l.sp);
                     return cudaGetLastError();
                 });
             });
@@ -223,7 +261,7 @@ cudaError_t launch_storage(const Launch &l)
     }
     if (l.kind == K_INIT) {
         return with_bool(l.pattern == 1, [&](auto AA) {
-            return with_model<S>(l.model, [&](auto C) {
+            return with_model<S, PART>(l.model, [&](auto C) {
                 return with_bool(l.force, [&](auto Fo) {
                     constexpr bool aa = decltype(AA)::value, fo = decltype(Fo)::value;
                     constexpr int c = decltype(C)::value;
@@ -238,67 +276,75 @@ cudaError_t launch_storage(const Launch &l)
             });
         });
     }
-    if (l.kind == K_ADJ) {
-        using R = typename Sto<S>::R;
-        return with_bool(l.force, [&](auto Fo) {
-            constexpr bool fo = decltype(Fo)::value;
-            if constexpr (std::is_same<R, float>::value && fo && L::Q == 19)
-                k_adjoint_bounded<L, R, fo, 5><<<l.grid, l.block, 0, l.stream>>>(l.sp, l.ap);
-            else
-                k_adjoint<L, R, fo><<<l.grid, l.block, 0, l.stream>>>(l.sp, l.ap);
-            return cudaGetLastError();
-        });
-    }
-    if (l.kind == K_SEED) {
-        return with_bool(l.force, [&](auto Fo) {
-            k_adjoint_seed<L, S, decltype(Fo)::value><<<l.grid, l.block, 0, l.stream>>>(l.sp, l.ap);
-            return cudaGetLastError();
-        });
-    }
-    if (l.kind == K_FLUSH) {
-        using R = typename Sto<S>::R;
-        k_adjoint_flush<R><<<l.grid, l.block, 0, l.stream>>>((R *)l.ap.gF, l.ap.dJdF, l.count);
-        return cudaGetLastError();
-    }
-    if (l.kind == K_MOMENTS) {
-        return with_bool(l.comp, [&](auto C) {
+    if constexpr (PART == 0) {  // the adjoint and the moments: not in the MRT units
+        if (l.kind == K_ADJ) {
+            using R = typename Sto<S>::R;
             return with_bool(l.force, [&](auto Fo) {
-                constexpr bool c = decltype(C)::value, fo = decltype(Fo)::value;
-                if constexpr (S == ST_F16S || S == ST_BF16S) {
-                    // 16-bit storage, the node's own slots: two nodes per
-                    // thread, one 32-bit load per slot
-                    if (l.pattern != FORM_STREAMED && l.sp.nx % 2 == 0) {
-                        MomParams mp = l.mp;
-                        mp.xseg = (l.sp.nx + 2 * kPairThreads - 1) / (2 * kPairThreads);
-                        mp.nseg = mp.xseg * l.sp.ny * l.sp.nz;
-                        const auto *s16 = (const unsigned short *)l.src;
-                        if (l.pattern == FORM_LOCAL)
-                            k_moments_pair<L, S, FORM_LOCAL, c, fo>
-                                <<<l.grid, kPairThreads, 0, l.stream>>>(s16, l.sp, mp);
-                        else
-                            k_moments_pair<L, S, FORM_SWAPPED, c, fo>
-                                <<<l.grid, kPairThreads, 0, l.stream>>>(s16, l.sp, mp);
-                        return cudaGetLastError();
-                    }
-                }
-                switch (l.pattern) {
-                case FORM_LOCAL:
-                    k_moments<L, S, FORM_LOCAL, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, l.sp, l.mp);
-                    break;
-                case FORM_SWAPPED:
-                    k_moments<L, S, FORM_SWAPPED, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, l.sp, l.mp);
-                    break;
-                default:
-                    k_moments<L, S, FORM_STREAMED, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, l.sp, l.mp);
-                    break;
-                }
+                constexpr bool fo = decltype(Fo)::value;
+                if constexpr (std::is_same<R, float>::value && fo && L::Q == 19)
+                    k_adjoint_bounded<L, R, fo, 5><<<l.grid, l.block, 0, l.stream>>>(l.sp, l.ap);
+                else
+                    k_adjoint<L, R, fo><<<l.grid, l.block, 0, l.stream>>>(l.sp, l.ap);
                 return cudaGetLastError();
             });
-        });
+        }
+        if (l.kind == K_SEED) {
+            return with_bool(l.force, [&](auto Fo) {
+                k_adjoint_seed<L, S, decltype(Fo)::value><<<l.grid, l.block, 0, l.stream>>>(l.sp, l.ap);
+                return cudaGetLastError();
+            });
+        }
+        if (l.kind == K_FLUSH) {
+            using R = typename Sto<S>::R;
+            k_adjoint_flush<R><<<l.grid, l.block, 0, l.stream>>>((R *)l.ap.gF, l.ap.dJdF, l.count);
+            return cudaGetLastError();
+        }
+        if (l.kind == K_MOMENTS) {
+            return with_bool(l.comp, [&](auto C) {
+                return with_bool(l.force, [&](auto Fo) {
+                    constexpr bool c = decltype(C)::value, fo = decltype(Fo)::value;
+                    if constexpr (S == ST_F16S || S == ST_BF16S) {
+                        // 16-bit storage, the node's own slots: two nodes per
+                        // thread, one 32-bit load per slot
+                        if (l.pattern != FORM_STREAMED && l.sp.nx % 2 == 0) {
+                            MomParams mp = l.mp;
+                            mp.xseg = (l.sp.nx + 2 * kPairThreads - 1) / (2 * kPairThreads);
+                            mp.nseg = mp.xseg * l.sp.ny * l.sp.nz;
+                            const auto *s16 = (const unsigned short *)l.src;
+                            if (l.pattern == FORM_LOCAL)
+                                k_moments_pair<L, S, FORM_LOCAL, c, fo>
+                                    <<<l.grid, kPairThreads, 0, l.stream>>>(s16, l.sp, mp);
+                            else
+                                k_moments_pair<L, S, FORM_SWAPPED, c, fo>
+                                    <<<l.grid, kPairThreads, 0, l.stream>>>(s16, l.sp, mp);
+                            return cudaGetLastError();
+                        }
+                    }
+                    switch (l.pattern) {
+                    case FORM_LOCAL:
+                        k_moments<L, S, FORM_LOCAL, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, l.sp, l.mp);
+                        break;
+                    case FORM_SWAPPED:
+                        k_moments<L, S, FORM_SWAPPED, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, l.sp, l.mp);
+                        break;
+                    default:
+                        k_moments<L, S, FORM_STREAMED, c, fo><<<l.grid, l.block, 0, l.stream>>>(src, l.sp, l.mp);
+                        break;
+                    }
+                    return cudaGetLastError();
+                });
+            });
+        }
     }
     return cudaErrorInvalidValue;
 }
 
 
+
+template <class L, int S>
+cudaError_t launch_mrt(const Launch &l)
+{
+    return launch_storage<L, S, 1>(l);
+}
 
 }  // namespace lbm
