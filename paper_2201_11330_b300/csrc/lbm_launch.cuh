@@ -60,9 +60,17 @@ constexpr int kPlainGatherMinBlocks = kPlainMinBlocks<L, S> > 0 ? kPlainMinBlock
                                       : (L::Q == 27 && S == ST_F32) ? 3
                                                                     : 0;
 
-// MRT step kernels: blocks per SM bound per pattern (0: the thread bound alone)
+// MRT step kernels: blocks per SM bound per pattern (0: the thread bound alone).
+// FP32 storage, measured at 512^3 (D3Q19) and 384^3 (D3Q27), ms per launch,
+// unbounded / bounded: D3Q19 at five (64 -> 48 registers, 32-72 B spilled)
+// pull 4.03 / 3.53, gather 4.69 / 4.32, local 3.43 / 3.49; D3Q27 at four
+// (80 -> 64 registers) pull 2.67 / 2.71, gather 3.40 / 2.96, local 2.62 /
+// 2.52.  One block more per SM was slower on every pattern.
 template <class L, int S, int PAT>
-constexpr int kMrtMinBlocks = 0;
+constexpr int kMrtMinBlocks = S != ST_F32   ? 0
+                              : L::Q == 19 ? (PAT == PAT_LOCAL ? 0 : 5)
+                              : L::Q == 27 ? (PAT == PAT_PULL ? 0 : 4)
+                                           : 0;
 
 template <class L, int S, int PART = 0>
 cudaError_t launch_storage(const Launch &l)
