@@ -347,11 +347,14 @@ __global__ void __launch_bounds__(256) k_step_geo(const typename Sto<S>::T *src,
 
 // The general kernel held to three blocks per SM (FP32 and 16-bit storage;
 // unbounded the D3Q27 form takes 88-90 registers, two blocks per SM, and its
-// node-list launch is memory-latency bound).
+// node-list launch is memory-latency bound).  D3Q27 with 16-bit storage: four
+// (64 registers; with the paired bulk kernel at seven, the 512x128x128 sphere
+// step went from 0.266 to 0.263 ms).
+template <class L, int S>
+constexpr int kGeoMinBlocks = (L::Q == 27 && (S == ST_F16S || S == ST_BF16S)) ? 4 : 3;
 template <class L, int S, int MODEL, bool FORCE, int MON>
-__global__ void __launch_bounds__(256, 3) k_step_geo_bounded(const typename Sto<S>::T *src,
-                                                              typename Sto<S>::T *dst,
-                                                              const StepParams p)
+__global__ void __launch_bounds__(256, (kGeoMinBlocks<L, S>))
+    k_step_geo_bounded(const typename Sto<S>::T *src, typename Sto<S>::T *dst, const StepParams p)
 {
     geo_kernel_body<L, S, MODEL, FORCE, MON>(src, dst, p);
 }

@@ -725,12 +725,14 @@ __global__ void __launch_bounds__(kPairThreads) k_moments_pair(const unsigned sh
 
 // The pull step of a box with per-face boundaries or obstacles on the pairs
 // the paired kernel can update (see k_step_skip).  MON: 0, 1 = monitor sums,
-// 2 = obstacle force (zero here).  Six blocks per SM, as the bounded D3Q27
-// kernels.
+// 2 = obstacle force (zero here).  Blocks per SM: D3Q27 seven (72 registers,
+// as the paired D3Q27 pull; eight spilled 356 bytes and was 16 % slower on the
+// sphere), D3Q19 six.
+template <class L>
+constexpr int kPairSkipMinBlocks = L::Q == 27 ? 7 : 6;
 template <class L, int S, int MODEL, bool FORCE, int MON>
-__global__ void __launch_bounds__(kPairThreads, 6) k_step_pair_skip(const unsigned short *src,
-                                                                 unsigned short *dst,
-                                                                 const StepParams p)
+__global__ void __launch_bounds__(kPairThreads, (kPairSkipMinBlocks<L>))
+    k_step_pair_skip(const unsigned short *src, unsigned short *dst, const StepParams p)
 {
     if constexpr (MON == 2) {
         if (threadIdx.x < kReduceVals)
