@@ -36,6 +36,7 @@ enum Form { FORM_LOCAL = 0, FORM_SWAPPED = 1, FORM_STREAMED = 2 };
 constexpr int kMaxQ = 27;
 constexpr int kReduceVals = 6;  // sum dP, momentum x/y/z, kinetic energy, max |u|^2
 constexpr int kPartialStride = 8;
+constexpr int kMonSlots = 256;  // threads of the largest block (monitor columns)
 
 template <class R>
 struct Coef {
@@ -506,29 +507,38 @@ __device__ __forceinline__ R warp_sum(R v);
 template <class R>
 __device__ __forceinline__ R warp_max(R v);
 
-// Block-wide monitor sums of the launch's nodes (warp in the kernel's
-// arithmetic, across warps in FP64, fixed order), written to
-// partials[block * 8 + k].  Every thread of the block must call it.
+// Block-wide monitor sums of the launch's nodes, written to
+// partials[block * kPartialStride + k] in FP64.  Each thread stores its six
+// values in shared memory (column k, row threadIdx.x); after a barrier, warp
+// w reduces the values k = w, w + nwarps, ... of the whole block in the
+// kernel's arithmetic (each lane its threads lane, lane + 32, ... in order,
+// then the warp tree; the maximum for k = 5), in a fixed order.  One store per
+// value and thread instead of a warp reduction per value and node: at 256^3
+// the monitor-fused AA local half went from 385.9 to 378.0 us.  (The gather
+// half keeps its own warp sums before the push stores: in this form it was
+// slower, 432.7 against 425.0 us.)  Every thread of the block must call it.
 template <class R>
 __device__ __forceinline__ void block_monitor(const R (&mon)[6], double *partials, size_t b)
 {
-    __shared__ double sh[32][6];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = (blockDim.x + 31) >> 5;
-    R w[6];
-    for (int k = 0; k < 5; ++k)
-        w[k] = warp_sum(mon[k]);
-    w[5] = warp_max(mon[5]);
-    if (lane == 0)
-        for (int k = 0; k < 6; ++k)
-            sh[warp][k] = double(w[k]);
+    __shared__ R col[6 * kMonSlots];
+    for (int k = 0; k < 6; ++k)
+        col[k * kMonSlots + threadIdx.x] = mon[k];
     __syncthreads();
-    if (threadIdx.x < 6) {
-        const int k = threadIdx.x;
-        double r = sh[0][k];
-        for (int i = 1; i < nwarps; ++i)
-            r = (k == 5) ? fmax(r, sh[i][k]) : r + sh[i][k];
-        partials[b * kPartialStride + k] = r;
+    const int lane = threadIdx.x & 31, nt = blockDim.x, nwarps = (nt + 31) >> 5;
+    for (int k = threadIdx.x >> 5; k < 6; k += nwarps) {
+        const R *c = col + k * kMonSlots;
+        R v = lane < nt ? c[lane] : R(0);
+        if (k == 5) {
+            for (int i = lane + 32; i < nt; i += 32)
+                v = max(v, c[i]);
+            v = warp_max(v);
+        } else {
+            for (int i = lane + 32; i < nt; i += 32)
+                v = o_add(v, c[i]);
+            v = warp_sum(v);
+        }
+        if (lane == 0)
+            partials[b * kPartialStride + k] = double(v);
     }
 }
 
